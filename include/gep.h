@@ -1,0 +1,163 @@
+/*
+ * gep.h - C ABI of a one-GPU (sm_103a) dense solver for the real symmetric-
+ * definite generalized eigenproblem
+ *
+ *     A y_k = lambda_k B y_k,   A Y = B Y Lambda,   Y^T B Y = I      (Eq. 1, Eq. 2)
+ *
+ * organised as Imachi & Hoshi decompose it (section 3.1): a *reducer*
+ * (Cholesky B = L L^T, Eq. 4 with L = U^T; two-sided reduction C = L^-1 A L^-T,
+ * Eq. 5; back-substitution Y = L^-T Z, Eq. 6) and an *SEP solver* (reduction
+ * of C to tridiagonal form, "TRD" in Table 3; a tridiagonal divide-and-conquer
+ * eigensolver, "D&C"; the Householder back-transformation, "BACK").  Each
+ * stage offers the variants of the paper's hybrid workflows (Table 1).
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are FP64, column-major, element (i,j) at X[i + j*ld], ld >= max(1,M).
+ *    Symmetric inputs are read from their LOWER triangle only.
+ *  - Every matrix/vector pointer is DEVICE memory owned by the caller; the library
+ *    never frees it.  Inputs documented as "overwritten" are modified in place.
+ *  - All calls enqueue work on the handle's stream and return without waiting
+ *    for the GPU, except gep_get_info() and the host-buffer variant
+ *    gep_solve_host(), which synchronise the stream.
+ *  - Return value: GEP_OK (0) on success; -i if argument i (1-based) is illegal
+ *    (checked on the host before anything is enqueued, LAPACK info < 0
+ *    convention); GEP_ERR_* codes below for other failures.
+ *  - Numerical status (B not positive definite, D&C not converged) is written to
+ *    device memory and read with gep_get_info(); once it is non-zero, later stages
+ *    of the same handle become no-ops until gep_reset_info().
+ */
+#ifndef GEP_H
+#define GEP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gep_handle_s* gep_handle_t;
+
+/* Return codes (negative values -1..-20 are "illegal argument i"). */
+#define GEP_OK 0
+#define GEP_ERR_CUDA (-100)        /* a CUDA runtime call failed                    */
+#define GEP_ERR_ALLOC (-101)       /* workspace too small / allocation failed      */
+#define GEP_ERR_NONFINITE (-102)   /* NaN or Inf found in an input matrix           */
+#define GEP_ERR_TIMEOUT (-103)     /* a bounded device-side wait gave up            */
+#define GEP_ERR_HANDLE (-104)      /* NULL or destroyed handle                      */
+#define GEP_ERR_UNSUPPORTED (-105) /* option combination not implemented            */
+
+/* Reducer variants (section 3.1, "ScaLAPACK style" / "ELPA style"). */
+#define GEP_RED_TWOSIDED 0     /* C = L^-1 A L^-T by triangular solves, L^-1 never formed */
+#define GEP_RED_EXPLICIT_INV 1 /* R = L^-1 formed explicitly, then C = R A R^T           */
+
+/* SEP-solver variants (section 3.1: conventional tridiagonalisation, or
+ * narrow-band reduction followed by band -> tridiagonal). */
+#define GEP_SEP_1STAGE 0
+#define GEP_SEP_2STAGE 1
+
+/* Arithmetic of the dense contractions. */
+#define GEP_PREC_FP64 0          /* FP64 throughout                                     */
+#define GEP_PREC_FP64_EMULATED 1 /* FP64-accurate products from split-BF16 tensor cores  */
+#define GEP_PREC_MIXED_REFINED 2 /* FP32-grade split-BF16 reducer + full->band, then FP64 refinement */
+
+typedef struct gep_options {
+  int reducer;      /* GEP_RED_*                                                  */
+  int sep;          /* GEP_SEP_*                                                  */
+  int bandwidth;    /* band width b for GEP_SEP_2STAGE (0 = library default)      */
+  int precision;    /* GEP_PREC_*                                                 */
+  int want_vectors; /* 1: eigenpairs (T_full); 0: eigenvalues only (T_evo)        */
+  int overwrite;    /* 1: A and B may be destroyed by gep_solve (saves two copies) */
+  int timers;       /* 1: record per-stage CUDA-event times (gep_get_stage_times) */
+} gep_options;
+
+/* Fills *o with the defaults: TWOSIDED, 1STAGE, b = 0, FP64, vectors, no overwrite, no timers. */
+void gep_default_options(gep_options* o);
+
+/* Creates a handle bound to `stream` (a cudaStream_t passed as void*; NULL = legacy
+ * default stream).  The handle owns a small device status block (allocated here). */
+int gep_create(gep_handle_t* h, void* stream);
+int gep_destroy(gep_handle_t h);
+int gep_set_stream(gep_handle_t h, void* stream);
+
+/* Bytes of device workspace gep_solve needs for order M with options o. */
+int gep_workspace_size(gep_handle_t h, int M, const gep_options* o, size_t* bytes);
+/* Hands the library caller-owned device workspace (256-byte aligned).  If none is
+ * set, or it is too small, gep_solve returns GEP_ERR_ALLOC. */
+int gep_set_workspace(gep_handle_t h, void* dptr, size_t bytes);
+
+/* ---- reducer (section 3.1 (b)) ------------------------------------------------
+ * gep_cholesky: Eq. 4.  B (lower) is overwritten by L with B = L L^T; the strict
+ *   upper triangle is not referenced.  Status k > 0 (gep_get_info) when the leading
+ *   minor of order k is not positive definite.
+ * gep_reduce: Eq. 5.  Expects L from gep_cholesky in B.  A (lower) is overwritten
+ *   by the full symmetric C = L^-1 A L^-T (both triangles written).
+ *   variant GEP_RED_EXPLICIT_INV additionally overwrites B's lower triangle with
+ *   R = L^-1 (ELPA style "R2"), which gep_backtransform then multiplies by.
+ * gep_backtransform: Eq. 6.  Z (M x ncol) is overwritten by Y = L^-T Z
+ *   (variant TWOSIDED: triangular solve with L in B) or Y = R^T Z (EXPLICIT_INV). */
+int gep_cholesky(gep_handle_t h, int M, double* B, int ldb);
+int gep_reduce(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, int variant);
+int gep_backtransform(gep_handle_t h, int M, int ncol, const double* B, int ldb, double* Z, int ldz,
+                      int variant);
+
+/* ---- SEP solver (section 3.1 (a); TRD / D&C / BACK of Table 3) ---------------
+ * sep_tridiag_1stage: Householder reduction C = Q T Q^T.  C (lower) is overwritten:
+ *   its strictly-lower part below the subdiagonal holds the reflectors v_k (unit
+ *   leading entry implied); d[M], e[M-1], tau[M-1] receive T and the reflector
+ *   scalars (H_k = I - tau_k v_k v_k^T, Q = H_0 H_1 ... H_{M-2}).
+ * sep_tridiag_eig: divide and conquer on (d, e).  w[M] receives the eigenvalues in
+ *   ascending order; if want_vectors, Z (M x M) receives the orthonormal eigenvectors
+ *   of T.  d and e are not modified.  want_vectors = 0 uses Sturm bisection.
+ * sep_backtransform: Z (M x ncol) is overwritten by Q Z using the reflectors left
+ *   in C by sep_tridiag_1stage (blocked compact-WY products). */
+int sep_tridiag_1stage(gep_handle_t h, int M, double* C, int ldc, double* d, double* e, double* tau);
+int sep_tridiag_eig(gep_handle_t h, int M, const double* d, const double* e, double* w, double* Z,
+                    int ldz, int want_vectors);
+int sep_backtransform(gep_handle_t h, int M, int ncol, const double* C, int ldc, const double* tau,
+                      double* Z, int ldz);
+
+/* ---- whole workflow ------------------------------------------------------------
+ * gep_solve: Eq. 2 for all M eigenpairs.  A, B (lower) are read and preserved unless
+ *   o->overwrite.  w[M] receives eigenvalues ascending; if o->want_vectors, Y (M x M,
+ *   ldy) receives B-orthonormal eigenvectors whose largest-magnitude entry is positive
+ *   (ties: lowest row index).  Uses the workspace set with gep_set_workspace. */
+int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, double* w, double* Y,
+              int ldy, const gep_options* o);
+
+/* Same as gep_solve but A, B, w, Y are HOST pointers (pinned or pageable): copies
+ * in, solves, copies out and synchronises.  Device memory comes from the workspace,
+ * which must be sized with gep_workspace_size(..., o) plus 2*M*M*8 + M*8 + M*M*8 bytes
+ * (gep_workspace_size_host gives the exact figure). */
+int gep_workspace_size_host(gep_handle_t h, int M, const gep_options* o, size_t* bytes);
+int gep_solve_host(gep_handle_t h, int M, const double* A, int lda, const double* B, int ldb,
+                   double* w, double* Y, int ldy, const gep_options* o);
+
+/* Synchronises the stream and returns the numerical status in *info:
+ *   0 ok; k in 1..M: leading minor k of B not positive definite (Eq. 4 failed);
+ *   M + j: divide and conquer failed on a subproblem; GEP_ERR_NONFINITE / GEP_ERR_TIMEOUT. */
+int gep_get_info(gep_handle_t h, int* info);
+int gep_reset_info(gep_handle_t h);
+
+/* Per-stage times (ms) of the last gep_solve with o->timers = 1:
+ * t[0] Cholesky (R1), t[1] reduction (R2), t[2] tridiagonalisation (TRD/BAND),
+ * t[3] tridiagonal eigensolver (D&C), t[4] Householder back-transform (BACK),
+ * t[5] back-substitution (R5 / Eq. 6).  Synchronises. */
+int gep_get_stage_times(gep_handle_t h, double t[6]);
+
+/* Number of kernels the library launched since gep_create / last reset. */
+long long gep_launch_count(gep_handle_t h, int reset);
+
+const char* gep_status_string(int code);
+
+/* ---- FP64 matrix product (the dense contraction every stage is built on) ------
+ * C = alpha op(A) op(B) + beta C, op = 'N' or 'T'; uplo 'F' (full) or 'L' (only
+ * entries i >= j of C are computed and written).  engine: GEP_PREC_FP64 (FP64 FMA)
+ * or GEP_PREC_FP64_EMULATED (split-BF16 tensor cores, FP64-accurate). */
+int gep_dgemm(gep_handle_t h, char transa, char transb, char uplo, int m, int n, int k, double alpha,
+              const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
+              int engine);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GEP_H */

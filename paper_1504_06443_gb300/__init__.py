@@ -1,0 +1,379 @@
+"""Python binding of libgep (include/gep.h): a one-GPU dense solver for the
+generalized eigenproblem A y = lambda B y (Imachi & Hoshi, Eq. 1-6).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels.  PyTorch provides device memory (the workspace is a torch tensor) and
+the stream.  If the compiled library is missing the import of a solver function
+raises; there is no CPU fallback.
+
+Matrices cross the boundary column-major.  Helpers accept any strided float64
+CUDA tensor: symmetric inputs may be passed row-major (their transpose is
+themselves); outputs come back as column-major views with the logical indices
+of the mathematics (Y[i, k] is component i of eigenvector k).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+__all__ = ["load", "solve", "solve_host", "cholesky", "reduce", "tridiag_1stage", "tridiag_eig",
+           "sep_backtransform", "gep_backtransform", "dgemm", "Handle", "default_handle",
+           "RED_TWOSIDED", "RED_EXPLICIT_INV", "SEP_1STAGE", "SEP_2STAGE", "PREC_FP64",
+           "PREC_FP64_EMULATED", "PREC_MIXED_REFINED", "GepError"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libgep.so")
+
+RED_TWOSIDED, RED_EXPLICIT_INV = 0, 1
+SEP_1STAGE, SEP_2STAGE = 0, 1
+PREC_FP64, PREC_FP64_EMULATED, PREC_MIXED_REFINED = 0, 1, 2
+
+_REDUCERS = {"twosided": RED_TWOSIDED, "explicit_inv": RED_EXPLICIT_INV}
+_SEPS = {"1stage": SEP_1STAGE, "2stage": SEP_2STAGE}
+_PRECS = {"fp64": PREC_FP64, "fp64_emulated": PREC_FP64_EMULATED, "mixed_refined": PREC_MIXED_REFINED}
+
+
+class GepError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = _lib_or_none().gep_status_string(code).decode() if _lib_or_none() else str(code)
+        super().__init__(f"{where} returned {code}: {msg}")
+
+
+class GepOptions(ctypes.Structure):
+    _fields_ = [("reducer", ctypes.c_int), ("sep", ctypes.c_int), ("bandwidth", ctypes.c_int),
+                ("precision", ctypes.c_int), ("want_vectors", ctypes.c_int), ("overwrite", ctypes.c_int),
+                ("timers", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SZ = ctypes.c_size_t
+
+
+def _lib_or_none():
+    return _lib
+
+
+def load():
+    """Loads the compiled library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgep.so not built ({LIB_PATH}); run paper_1504_06443_gb300.build.build() "
+                               "or __graft_entry__.build() first")
+        lib = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "gep_default_options": (None, [ctypes.POINTER(GepOptions)]),
+            "gep_create": (_I, [ctypes.POINTER(_P), _P]),
+            "gep_destroy": (_I, [_P]),
+            "gep_set_stream": (_I, [_P, _P]),
+            "gep_workspace_size": (_I, [_P, _I, ctypes.POINTER(GepOptions), ctypes.POINTER(_SZ)]),
+            "gep_workspace_size_host": (_I, [_P, _I, ctypes.POINTER(GepOptions), ctypes.POINTER(_SZ)]),
+            "gep_set_workspace": (_I, [_P, _P, _SZ]),
+            "gep_cholesky": (_I, [_P, _I, _P, _I]),
+            "gep_reduce": (_I, [_P, _I, _P, _I, _P, _I, _I]),
+            "gep_backtransform": (_I, [_P, _I, _I, _P, _I, _P, _I, _I]),
+            "sep_tridiag_1stage": (_I, [_P, _I, _P, _I, _P, _P, _P]),
+            "sep_tridiag_eig": (_I, [_P, _I, _P, _P, _P, _P, _I, _I]),
+            "sep_backtransform": (_I, [_P, _I, _I, _P, _I, _P, _P, _I]),
+            "gep_solve": (_I, [_P, _I, _P, _I, _P, _I, _P, _P, _I, ctypes.POINTER(GepOptions)]),
+            "gep_solve_host": (_I, [_P, _I, _P, _I, _P, _I, _P, _P, _I, ctypes.POINTER(GepOptions)]),
+            "gep_get_info": (_I, [_P, ctypes.POINTER(_I)]),
+            "gep_reset_info": (_I, [_P]),
+            "gep_get_stage_times": (_I, [_P, ctypes.POINTER(_D)]),
+            "gep_launch_count": (ctypes.c_longlong, [_P, _I]),
+            "gep_status_string": (ctypes.c_char_p, [_I]),
+            "gep_dgemm": (_I, [_P, ctypes.c_char, ctypes.c_char, ctypes.c_char, _I, _I, _I, _D, _P, _I, _P, _I,
+                               _D, _P, _I, _I]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise GepError(rc, where)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def colmajor(t):
+    """A float64 CUDA tensor with the same logical values, stored column-major (strides (1, m))."""
+    torch = _torch()
+    t = t.to(dtype=torch.float64)
+    if t.dim() == 2 and t.stride(0) == 1 and t.stride(1) >= max(1, t.shape[0]):
+        return t
+    return t.t().contiguous().t()
+
+
+def _ld(t):
+    return max(1, t.stride(1)) if t.dim() == 2 else max(1, t.shape[0])
+
+
+def _sym_ptr_ld(t):
+    """Pointer + leading dimension for a symmetric matrix argument (any 2-D memory order)."""
+    if t.stride(0) == 1:
+        return _ptr(t), max(1, t.stride(1))
+    if t.stride(1) == 1:
+        return _ptr(t), max(1, t.stride(0))  # row-major buffer = transpose = itself
+    raise ValueError("symmetric matrix argument must have a unit stride in one dimension")
+
+
+class Handle:
+    """A libgep handle bound to one CUDA stream, with a torch-allocated workspace."""
+
+    def __init__(self, stream=None, device=None):
+        torch = _torch()
+        self.lib = load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib.gep_create(ctypes.byref(h), ctypes.c_void_p(self.stream.cuda_stream)), "gep_create")
+        self.h = h
+        self.ws = None
+
+    def close(self):
+        if self.h:
+            self.lib.gep_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def ensure_workspace(self, nbytes):
+        torch = _torch()
+        if self.ws is None or self.ws.numel() < nbytes:
+            self.ws = None
+            self.ws = torch.empty(max(int(nbytes), 256) + 256, dtype=torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        aligned = (base + 255) & ~255
+        _check(self.lib.gep_set_workspace(self.h, ctypes.c_void_p(aligned), self.ws.numel() - (aligned - base)),
+               "gep_set_workspace")
+
+    def info(self):
+        v = _I()
+        _check(self.lib.gep_get_info(self.h, ctypes.byref(v)), "gep_get_info")
+        return v.value
+
+    def reset_info(self):
+        _check(self.lib.gep_reset_info(self.h), "gep_reset_info")
+
+    def stage_times(self):
+        t = (_D * 6)()
+        _check(self.lib.gep_get_stage_times(self.h, t), "gep_get_stage_times")
+        return list(t)
+
+    def launches(self, reset=False):
+        return int(self.lib.gep_launch_count(self.h, 1 if reset else 0))
+
+
+_handles = {}
+
+
+def default_handle():
+    torch = _torch()
+    key = (torch.cuda.current_device(), torch.cuda.current_stream().cuda_stream)
+    h = _handles.get(key)
+    if h is None:
+        h = Handle()
+        _handles[key] = h
+    return h
+
+
+def make_options(reducer="twosided", sep="1stage", precision="fp64", want_vectors=True, overwrite=False,
+                 timers=False, bandwidth=0):
+    o = GepOptions()
+    load().gep_default_options(ctypes.byref(o))
+    o.reducer = _REDUCERS[reducer] if isinstance(reducer, str) else int(reducer)
+    o.sep = _SEPS[sep] if isinstance(sep, str) else int(sep)
+    o.precision = _PRECS[precision] if isinstance(precision, str) else int(precision)
+    o.want_vectors = 1 if want_vectors else 0
+    o.overwrite = 1 if overwrite else 0
+    o.timers = 1 if timers else 0
+    o.bandwidth = int(bandwidth)
+    return o
+
+
+def workspace_bytes(M, handle=None, **opts):
+    h = handle or default_handle()
+    o = make_options(**opts)
+    n = _SZ()
+    _check(h.lib.gep_workspace_size(h.h, int(M), ctypes.byref(o), ctypes.byref(n)), "gep_workspace_size")
+    return n.value
+
+
+def solve(A, B, reducer="twosided", sep="1stage", precision="fp64", want_vectors=True, overwrite=False,
+          timers=False, bandwidth=0, handle=None, out=None):
+    """All eigenpairs of A y = lambda B y (A, B symmetric float64 CUDA tensors, B SPD).
+
+    Returns (w, Y, info): w ascending, Y (column-major view) B-orthonormal or None.
+    info != 0 reports a numerical failure (k: B's leading minor k not positive definite)."""
+    torch = _torch()
+    h = handle or default_handle()
+    M = int(A.shape[0])
+    o = make_options(reducer, sep, precision, want_vectors, overwrite, timers, bandwidth)
+    n = _SZ()
+    _check(h.lib.gep_workspace_size(h.h, M, ctypes.byref(o), ctypes.byref(n)), "gep_workspace_size")
+    h.ensure_workspace(n.value)
+    pa, lda = _sym_ptr_ld(A)
+    pb, ldb = _sym_ptr_ld(B)
+    if out is not None:
+        w, Yt = out
+    else:
+        w = torch.empty(M, dtype=torch.float64, device=A.device)
+        Yt = torch.empty((M, M), dtype=torch.float64, device=A.device) if want_vectors else None
+    _check(h.lib.gep_solve(h.h, M, pa, lda, pb, ldb, _ptr(w), _ptr(Yt), max(1, M), ctypes.byref(o)), "gep_solve")
+    info = h.info()
+    return w, (Yt.t() if Yt is not None else None), info
+
+
+def solve_async(A, B, w, Yt, opts, handle):
+    """Enqueue-only variant used by the benchmark: no synchronisation, no allocation."""
+    pa, lda = _sym_ptr_ld(A)
+    pb, ldb = _sym_ptr_ld(B)
+    _check(handle.lib.gep_solve(handle.h, int(A.shape[0]), pa, lda, pb, ldb, _ptr(w), _ptr(Yt), max(1, A.shape[0]),
+                                ctypes.byref(opts)), "gep_solve")
+
+
+def solve_host(A_np, B_np, want_vectors=True, handle=None, **opts):
+    """Host numpy arrays in and out (copies inside the library).  Returns (w, Y)."""
+    import numpy as np
+    h = handle or default_handle()
+    M = int(A_np.shape[0])
+    o = make_options(want_vectors=want_vectors, **opts)
+    n = _SZ()
+    _check(h.lib.gep_workspace_size_host(h.h, M, ctypes.byref(o), ctypes.byref(n)), "gep_workspace_size_host")
+    h.ensure_workspace(n.value)
+    A = np.ascontiguousarray(A_np, dtype=np.float64)
+    B = np.ascontiguousarray(B_np, dtype=np.float64)
+    w = np.empty(M)
+    Y = np.empty((M, M), order="F") if want_vectors else None
+    _check(h.lib.gep_solve_host(h.h, M, A.ctypes.data_as(_P), max(1, M), B.ctypes.data_as(_P), max(1, M),
+                                w.ctypes.data_as(_P), Y.ctypes.data_as(_P) if Y is not None else None,
+                                max(1, M), ctypes.byref(o)), "gep_solve_host")
+    return w, Y, h.info()
+
+
+# ------------------------------------------------------------------ stages
+
+def cholesky(B, handle=None):
+    """Eq. 4: returns (L column-major, info)."""
+    h = handle or default_handle()
+    L = colmajor(B.clone())
+    M = L.shape[0]
+    h.ensure_workspace(_stage_ws(M))
+    h.reset_info()
+    _check(h.lib.gep_cholesky(h.h, M, _ptr(L), _ld(L)), "gep_cholesky")
+    return L, h.info()
+
+
+def _stage_ws(M, ncol=None):
+    ncol = M if ncol is None else ncol
+    return 8 * (3 * M * M + 2 * M * 128 + ((M + 127) // 128) * 128 * 128 + 64 * M + 1024) + 8 * M * ncol + 4096 + \
+        8 * (M * 64 * 2 + ((M + 63) // 64) * (M + 64) + 64 * 64 * 3)
+
+
+def reduce(A, L, variant="twosided", handle=None):
+    """Eq. 5: (C, L_or_R).  For 'explicit_inv' the returned second matrix is R = L^-1."""
+    h = handle or default_handle()
+    C = colmajor(A.clone())
+    Lc = colmajor(L.clone())
+    M = C.shape[0]
+    h.ensure_workspace(_stage_ws(M))
+    _check(h.lib.gep_reduce(h.h, M, _ptr(C), _ld(C), _ptr(Lc), _ld(Lc), _REDUCERS[variant]), "gep_reduce")
+    return C, Lc
+
+
+def gep_backtransform(LR, Z, variant="twosided", handle=None):
+    """Eq. 6: Y = L^-T Z (twosided) or Y = R^T Z (explicit_inv)."""
+    h = handle or default_handle()
+    Y = colmajor(Z.clone())
+    Lc = colmajor(LR)
+    M, ncol = Y.shape
+    h.ensure_workspace(_stage_ws(M, ncol))
+    _check(h.lib.gep_backtransform(h.h, M, ncol, _ptr(Lc), _ld(Lc), _ptr(Y), _ld(Y), _REDUCERS[variant]),
+           "gep_backtransform")
+    return Y
+
+
+def tridiag_1stage(C, handle=None):
+    """Householder tridiagonalisation: (d, e, tau, C_with_reflectors)."""
+    torch = _torch()
+    h = handle or default_handle()
+    Cc = colmajor(C.clone())
+    M = Cc.shape[0]
+    d = torch.empty(M, dtype=torch.float64, device=C.device)
+    e = torch.zeros(max(M, 1), dtype=torch.float64, device=C.device)
+    tau = torch.zeros(max(M, 1), dtype=torch.float64, device=C.device)
+    h.ensure_workspace(_stage_ws(M))
+    _check(h.lib.sep_tridiag_1stage(h.h, M, _ptr(Cc), _ld(Cc), _ptr(d), _ptr(e), _ptr(tau)), "sep_tridiag_1stage")
+    return d, e[: max(M - 1, 0)], tau[: max(M - 1, 0)], Cc
+
+
+def tridiag_eig(d, e, want_vectors=True, handle=None):
+    """Divide and conquer (or bisection when want_vectors=False): (w ascending, Z or None, info)."""
+    torch = _torch()
+    h = handle or default_handle()
+    M = int(d.shape[0])
+    dd = d.to(torch.float64).contiguous()
+    ee = torch.zeros(max(M, 1), dtype=torch.float64, device=d.device)
+    if M > 1:
+        ee[: M - 1] = e[: M - 1]
+    w = torch.empty(M, dtype=torch.float64, device=d.device)
+    Zt = torch.empty((M, M), dtype=torch.float64, device=d.device) if want_vectors else None
+    h.ensure_workspace(_stage_ws(M))
+    h.reset_info()
+    _check(h.lib.sep_tridiag_eig(h.h, M, _ptr(dd), _ptr(ee), _ptr(w), _ptr(Zt), max(1, M), 1 if want_vectors else 0),
+           "sep_tridiag_eig")
+    return w, (Zt.t() if Zt is not None else None), h.info()
+
+
+def sep_backtransform(C_refl, tau, Z, handle=None):
+    """Z <- Q Z with the reflectors of tridiag_1stage."""
+    torch = _torch()
+    h = handle or default_handle()
+    Y = colmajor(Z.clone())
+    Cc = colmajor(C_refl)
+    M, ncol = Y.shape
+    tt = torch.zeros(max(M, 1), dtype=torch.float64, device=Z.device)
+    if M > 1:
+        tt[: M - 1] = tau[: M - 1]
+    h.ensure_workspace(_stage_ws(M, ncol))
+    _check(h.lib.sep_backtransform(h.h, M, ncol, _ptr(Cc), _ld(Cc), _ptr(tt), _ptr(Y), _ld(Y)), "sep_backtransform")
+    return Y
+
+
+def dgemm(A, B, transa="N", transb="N", alpha=1.0, beta=0.0, C=None, uplo="F", engine="fp64", handle=None):
+    """C = alpha op(A) op(B) + beta C on the library's GEMM engine (column-major views)."""
+    torch = _torch()
+    h = handle or default_handle()
+    Ac, Bc = colmajor(A), colmajor(B)
+    m = Ac.shape[1] if transa == "T" else Ac.shape[0]
+    k = Ac.shape[0] if transa == "T" else Ac.shape[1]
+    n = Bc.shape[0] if transb == "T" else Bc.shape[1]
+    Cc = colmajor(C.clone()) if C is not None else torch.zeros((n, m), dtype=torch.float64, device=A.device).t()
+    _check(h.lib.gep_dgemm(h.h, transa.encode(), transb.encode(), uplo.encode(), m, n, k, float(alpha), _ptr(Ac),
+                           _ld(Ac), _ptr(Bc), _ld(Bc), float(beta), _ptr(Cc), _ld(Cc), _PRECS[engine]), "gep_dgemm")
+    return Cc

@@ -1,0 +1,456 @@
+// C ABI (include/gep.h): handle, workspace, stage entry points and the whole
+// GEP workflow of section 3.1 (reducer -> SEP solver -> back-transformation).
+// Host code here only validates arguments, carves the caller's workspace and
+// enqueues kernels; no step of the method runs on the host.
+#include <string.h>
+
+#include "gep_internal.cuh"
+
+using namespace gep;
+
+namespace {
+
+constexpr int NB = 128;  // diagonal block order of the triangular kernels (tri.cu)
+
+bool handle_ok(gep_handle_t h) { return h != nullptr && h->magic == 0x6e70; }
+
+struct SolveLayout {
+  size_t Cw, Lw, invD, vec, uni, end;  // byte offsets
+  size_t uni_bytes;
+};
+
+size_t r256(size_t x) { return align256(x); }
+
+size_t invd_bytes(int M) {
+  size_t nblk = (M + NB - 1) / NB;
+  return (nblk * NB * NB + (size_t)M * NB) * sizeof(double);
+}
+
+size_t union_bytes(int M, const gep_options* o) {
+  size_t mm = (size_t)M * M * sizeof(double);
+  size_t tmpb = (size_t)NB * M * sizeof(double);
+  size_t red = (o->reducer == GEP_RED_EXPLICIT_INV) ? r256(mm) + r256(mm) + r256(tmpb) : r256(mm) + r256(tmpb);
+  size_t tri = tridiag_ws_elems(M) * sizeof(double);
+  size_t dc = o->want_vectors ? dc_ws_bytes(M) : 0;
+  size_t bt = o->want_vectors ? backtransform_ws_elems(M, M) * sizeof(double) : 0;
+  size_t r3 = o->want_vectors ? (r256(tmpb) + (o->reducer == GEP_RED_EXPLICIT_INV ? r256(mm) : 0)) : 0;
+  size_t u = red;
+  if (tri > u) u = tri;
+  if (dc > u) u = dc;
+  if (bt > u) u = bt;
+  if (r3 > u) u = r3;
+  return r256(u);
+}
+
+SolveLayout layout(int M, const gep_options* o) {
+  SolveLayout L;
+  size_t mm = (size_t)M * M * sizeof(double);
+  size_t off = 0;
+  L.Cw = off; off += o->overwrite ? 0 : r256(mm);
+  L.Lw = off; off += o->overwrite ? 0 : r256(mm);
+  L.invD = off; off += r256(invd_bytes(M));
+  L.vec = off; off += r256((size_t)3 * (M + 1) * sizeof(double));
+  L.uni = off;
+  L.uni_bytes = union_bytes(M, o);
+  off += L.uni_bytes;
+  L.end = off;
+  return L;
+}
+
+int check_opts(const gep_options* o) {
+  if (!o) return -1;
+  if (o->reducer != GEP_RED_TWOSIDED && o->reducer != GEP_RED_EXPLICIT_INV) return GEP_ERR_UNSUPPORTED;
+  if (o->sep != GEP_SEP_1STAGE) return GEP_ERR_UNSUPPORTED;
+  if (o->precision != GEP_PREC_FP64 && o->precision != GEP_PREC_FP64_EMULATED) return GEP_ERR_UNSUPPORTED;
+  return GEP_OK;
+}
+
+int reset_status(gep_handle_t h) {
+  GEP_CUDA(cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), h->stream));
+  return GEP_OK;
+}
+
+void mark(gep_handle_t h, const gep_options* o, int i) {
+  if (o->timers) cudaEventRecord(h->ev[i], h->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+void gep_default_options(gep_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->reducer = GEP_RED_TWOSIDED;
+  o->sep = GEP_SEP_1STAGE;
+  o->precision = GEP_PREC_FP64;
+  o->want_vectors = 1;
+}
+
+int gep_create(gep_handle_t* out, void* stream) {
+  if (!out) return -1;
+  *out = nullptr;
+  gep_handle_t h = new gep_handle_s();
+  h->stream = (cudaStream_t)stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaMalloc((void**)&h->d_status, 256) != cudaSuccess) { delete h; return GEP_ERR_CUDA; }
+  if (cudaMemset(h->d_status, 0, 256) != cudaSuccess) { cudaFree(h->d_status); delete h; return GEP_ERR_CUDA; }
+  for (int i = 0; i < 8; ++i) cudaEventCreate(&h->ev[i]);
+  *out = h;
+  return GEP_OK;
+}
+
+int gep_destroy(gep_handle_t h) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  cudaStreamSynchronize(h->stream);
+  for (int i = 0; i < 8; ++i) cudaEventDestroy(h->ev[i]);
+  cudaFree(h->d_status);
+  h->magic = 0;
+  delete h;
+  return GEP_OK;
+}
+
+int gep_set_stream(gep_handle_t h, void* stream) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  h->stream = (cudaStream_t)stream;
+  return GEP_OK;
+}
+
+int gep_workspace_size(gep_handle_t h, int M, const gep_options* o, size_t* bytes) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (M < 0) return -2;
+  if (!o) return -3;
+  if (!bytes) return -4;
+  *bytes = layout(M, o).end;
+  return GEP_OK;
+}
+
+int gep_set_workspace(gep_handle_t h, void* dptr, size_t bytes) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (dptr == nullptr && bytes != 0) return -2;
+  if (((uintptr_t)dptr & 255) != 0) return -2;
+  h->ws = (char*)dptr;
+  h->ws_bytes = bytes;
+  return GEP_OK;
+}
+
+int gep_get_info(gep_handle_t h, int* info) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (!info) return -2;
+  int st[2] = {0, 0};
+  GEP_CUDA(cudaStreamSynchronize(h->stream));
+  GEP_CUDA(cudaMemcpy(st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  *info = st[1] != 0 ? st[1] : st[0];
+  return GEP_OK;
+}
+
+int gep_reset_info(gep_handle_t h) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  return reset_status(h);
+}
+
+long long gep_launch_count(gep_handle_t h, int reset) {
+  if (!handle_ok(h)) return -1;
+  long long n = h->launches;
+  if (reset) h->launches = 0;
+  return n;
+}
+
+int gep_get_stage_times(gep_handle_t h, double t[6]) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (!t) return -2;
+  if (!h->timers_recorded) return GEP_ERR_UNSUPPORTED;
+  GEP_CUDA(cudaEventSynchronize(h->ev[6]));
+  for (int i = 0; i < 6; ++i) {
+    float ms = 0.f;
+    GEP_CUDA(cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]));
+    t[i] = ms;
+  }
+  return GEP_OK;
+}
+
+const char* gep_status_string(int code) {
+  switch (code) {
+    case GEP_OK: return "ok";
+    case GEP_ERR_CUDA: return "CUDA runtime error";
+    case GEP_ERR_ALLOC: return "workspace missing or too small";
+    case GEP_ERR_NONFINITE: return "NaN or Inf in an input matrix";
+    case GEP_ERR_TIMEOUT: return "a bounded device-side wait gave up";
+    case GEP_ERR_HANDLE: return "invalid handle";
+    case GEP_ERR_UNSUPPORTED: return "option combination not implemented";
+    default: break;
+  }
+  if (code < 0 && code >= -20) return "illegal argument";
+  if (code > 0) return "numerical failure (see gep_get_info)";
+  return "unknown status";
+}
+
+int gep_dgemm(gep_handle_t h, char transa, char transb, char uplo, int m, int n, int k, double alpha,
+              const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
+              int engine) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  bool ta = (transa == 'T' || transa == 't'), tb = (transb == 'T' || transb == 't');
+  if (!ta && transa != 'N' && transa != 'n') return -2;
+  if (!tb && transb != 'N' && transb != 'n') return -3;
+  if (uplo != 'F' && uplo != 'f' && uplo != 'L' && uplo != 'l') return -4;
+  if (m < 0) return -5;
+  if (n < 0) return -6;
+  if (k < 0) return -7;
+  if (lda < (ta ? (k > 1 ? k : 1) : (m > 1 ? m : 1))) return -10;
+  if (ldb < (tb ? (n > 1 ? n : 1) : (k > 1 ? k : 1))) return -12;
+  if (ldc < (m > 1 ? m : 1)) return -15;
+  if (engine != GEP_PREC_FP64 && engine != GEP_PREC_FP64_EMULATED && engine != GEP_PREC_MIXED_REFINED) return -16;
+  return dgemm(h, transa, transb, uplo, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, engine);
+}
+
+int gep_cholesky(gep_handle_t h, int M, double* B, int ldb) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (M < 0) return -2;
+  if (M > 0 && !B) return -3;
+  if (ldb < (M > 1 ? M : 1)) return -4;
+  if (M == 0) return GEP_OK;
+  Arena ar(h->ws, h->ws_bytes);
+  double* invD = ar.take<double>(invd_bytes(M) / sizeof(double));
+  if (!ar.ok) return GEP_ERR_ALLOC;
+  return cholesky(h, M, B, ldb, invD, GEP_PREC_FP64);
+}
+
+int gep_reduce(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, int variant) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (M < 0) return -2;
+  if (M > 0 && !A) return -3;
+  if (lda < (M > 1 ? M : 1)) return -4;
+  if (M > 0 && !B) return -5;
+  if (ldb < (M > 1 ? M : 1)) return -6;
+  if (variant != GEP_RED_TWOSIDED && variant != GEP_RED_EXPLICIT_INV) return -7;
+  if (M == 0) return GEP_OK;
+  Arena ar(h->ws, h->ws_bytes);
+  double* invD = ar.take<double>(invd_bytes(M) / sizeof(double));
+  double* X = ar.take<double>((size_t)M * M);
+  double* tmp = ar.take<double>((size_t)M * M + (size_t)NB * M);
+  if (!ar.ok) return GEP_ERR_ALLOC;
+  GEP_CHECK(tri_inv_diag_blocks(h, M, B, ldb, invD, NB));
+  if (variant == GEP_RED_TWOSIDED) return reduce_twosided(h, M, A, lda, B, ldb, invD, X, tmp, GEP_PREC_FP64);
+  return reduce_explicit_inv(h, M, A, lda, B, ldb, invD, X, tmp, GEP_PREC_FP64);
+}
+
+int gep_backtransform(gep_handle_t h, int M, int ncol, const double* B, int ldb, double* Z, int ldz,
+                      int variant) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (M < 0) return -2;
+  if (ncol < 0) return -3;
+  if (M > 0 && !B) return -4;
+  if (ldb < (M > 1 ? M : 1)) return -5;
+  if (M > 0 && ncol > 0 && !Z) return -6;
+  if (ldz < (M > 1 ? M : 1)) return -7;
+  if (variant != GEP_RED_TWOSIDED && variant != GEP_RED_EXPLICIT_INV) return -8;
+  if (M == 0 || ncol == 0) return GEP_OK;
+  Arena ar(h->ws, h->ws_bytes);
+  if (variant == GEP_RED_TWOSIDED) {
+    double* invD = ar.take<double>(invd_bytes(M) / sizeof(double));
+    double* tmp = ar.take<double>((size_t)NB * ncol);
+    if (!ar.ok) return GEP_ERR_ALLOC;
+    GEP_CHECK(tri_inv_diag_blocks(h, M, B, ldb, invD, NB));
+    return trsm_llt(h, M, ncol, B, ldb, invD, NB, Z, ldz, tmp, GEP_PREC_FP64);
+  }
+  double* T = ar.take<double>((size_t)M * ncol);
+  double* R = ar.take<double>((size_t)M * M);
+  if (!ar.ok) return GEP_ERR_ALLOC;
+  // Y = R^T Z with R the lower triangle of B (its upper part is not referenced)
+  GEP_CHECK(set_matrix(h, M, M, 0.0, 0.0, R, M));
+  GEP_CHECK(copy_lower(h, M, B, ldb, R, M));
+  GEP_CHECK(dgemm(h, 'T', 'N', 'F', M, ncol, M, 1.0, R, M, Z, ldz, 0.0, T, M, GEP_PREC_FP64));
+  return copy_matrix(h, M, ncol, T, M, Z, ldz);
+}
+
+int sep_tridiag_1stage(gep_handle_t h, int M, double* C, int ldc, double* d, double* e, double* tau) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (M < 0) return -2;
+  if (M > 0 && !C) return -3;
+  if (ldc < (M > 1 ? M : 1)) return -4;
+  if (M > 0 && !d) return -5;
+  if (M > 1 && !e) return -6;
+  if (M > 1 && !tau) return -7;
+  if (M == 0) return GEP_OK;
+  Arena ar(h->ws, h->ws_bytes);
+  size_t n = tridiag_ws_elems(M);
+  double* ws = ar.take<double>(n);
+  if (!ar.ok) return GEP_ERR_ALLOC;
+  return tridiag_1stage(h, M, C, ldc, d, e, tau, ws, n, GEP_PREC_FP64);
+}
+
+int sep_tridiag_eig(gep_handle_t h, int M, const double* d, const double* e, double* w, double* Z,
+                    int ldz, int want_vectors) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (M < 0) return -2;
+  if (M > 0 && !d) return -3;
+  if (M > 1 && !e) return -4;
+  if (M > 0 && !w) return -5;
+  if (want_vectors && M > 0 && !Z) return -6;
+  if (want_vectors && ldz < (M > 1 ? M : 1)) return -7;
+  if (M == 0) return GEP_OK;
+  if (!want_vectors) return tridiag_eig_bisect(h, M, d, e, w);
+  Arena ar(h->ws, h->ws_bytes);
+  size_t nb = dc_ws_bytes(M);
+  double* ws = (double*)ar.take<char>(nb);
+  if (!ar.ok) return GEP_ERR_ALLOC;
+  return tridiag_eig_dc(h, M, d, e, w, Z, ldz, ws, nb, GEP_PREC_FP64);
+}
+
+int sep_backtransform(gep_handle_t h, int M, int ncol, const double* C, int ldc, const double* tau,
+                      double* Z, int ldz) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (M < 0) return -2;
+  if (ncol < 0) return -3;
+  if (M > 0 && !C) return -4;
+  if (ldc < (M > 1 ? M : 1)) return -5;
+  if (M > 1 && !tau) return -6;
+  if (M > 0 && ncol > 0 && !Z) return -7;
+  if (ldz < (M > 1 ? M : 1)) return -8;
+  if (M <= 1 || ncol == 0) return GEP_OK;
+  Arena ar(h->ws, h->ws_bytes);
+  size_t n = backtransform_ws_elems(M, ncol);
+  double* ws = ar.take<double>(n);
+  if (!ar.ok) return GEP_ERR_ALLOC;
+  return backtransform_q(h, M, ncol, C, ldc, tau, Z, ldz, ws, n, GEP_PREC_FP64);
+}
+
+int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, double* w, double* Y,
+              int ldy, const gep_options* o) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (M < 0) return -2;
+  if (M > 0 && !A) return -3;
+  if (lda < (M > 1 ? M : 1)) return -4;
+  if (M > 0 && !B) return -5;
+  if (ldb < (M > 1 ? M : 1)) return -6;
+  if (M > 0 && !w) return -7;
+  if (!o) return -10;
+  if (o->want_vectors && M > 0 && !Y) return -8;
+  if (o->want_vectors && ldy < (M > 1 ? M : 1)) return -9;
+  GEP_CHECK(check_opts(o));
+  if (M == 0) return GEP_OK;
+  SolveLayout Ly = layout(M, o);
+  if (h->ws == nullptr || h->ws_bytes < Ly.end) return GEP_ERR_ALLOC;
+  const int eng = o->precision;
+  char* base = h->ws;
+  double* Cw = o->overwrite ? A : (double*)(base + Ly.Cw);
+  int ldcw = o->overwrite ? lda : M;
+  double* Lw = o->overwrite ? B : (double*)(base + Ly.Lw);
+  int ldlw = o->overwrite ? ldb : M;
+  double* invD = (double*)(base + Ly.invD);
+  double* dvec = (double*)(base + Ly.vec);
+  double* evec = dvec + (M + 1);
+  double* tvec = evec + (M + 1);
+  char* uni = base + Ly.uni;
+  h->timers_recorded = false;
+
+  GEP_CHECK(reset_status(h));
+  GEP_CHECK(scan_nonfinite(h, M, A, lda));
+  GEP_CHECK(scan_nonfinite(h, M, B, ldb));
+  if (!o->overwrite) {
+    GEP_CHECK(copy_lower(h, M, A, lda, Cw, ldcw));
+    GEP_CHECK(copy_lower(h, M, B, ldb, Lw, ldlw));
+  }
+  mark(h, o, 0);
+  GEP_CHECK(cholesky(h, M, Lw, ldlw, invD, eng));  // R1
+  mark(h, o, 1);
+  {
+    double* X = (double*)uni;
+    double* tmp = (double*)(uni + r256((size_t)M * M * sizeof(double)));
+    if (o->reducer == GEP_RED_TWOSIDED)
+      GEP_CHECK(reduce_twosided(h, M, Cw, ldcw, Lw, ldlw, invD, X, tmp, eng));  // R2
+    else {
+      GEP_CHECK(reduce_explicit_inv(h, M, Cw, ldcw, Lw, ldlw, invD, X, tmp, eng));
+      GEP_CHECK(zero_upper(h, M, Lw, ldlw));  // R is used as a full matrix by Eq. 6 below
+    }
+  }
+  mark(h, o, 2);
+  GEP_CHECK(tridiag_1stage(h, M, Cw, ldcw, dvec, evec, tvec, (double*)uni, Ly.uni_bytes / sizeof(double), eng));
+  mark(h, o, 3);
+  if (!o->want_vectors) {
+    GEP_CHECK(tridiag_eig_bisect(h, M, dvec, evec, w));
+    mark(h, o, 4);
+    mark(h, o, 5);
+    mark(h, o, 6);
+    h->timers_recorded = o->timers != 0;
+    return GEP_OK;
+  }
+  GEP_CHECK(tridiag_eig_dc(h, M, dvec, evec, w, Y, ldy, (double*)uni, Ly.uni_bytes, eng));  // D&C
+  mark(h, o, 4);
+  GEP_CHECK(backtransform_q(h, M, M, Cw, ldcw, tvec, Y, ldy, (double*)uni, Ly.uni_bytes / sizeof(double), eng));
+  mark(h, o, 5);
+  if (o->reducer == GEP_RED_TWOSIDED) {
+    GEP_CHECK(trsm_llt(h, M, M, Lw, ldlw, invD, NB, Y, ldy, (double*)uni, eng));  // Eq. 6
+  } else {
+    double* T = (double*)uni;
+    GEP_CHECK(dgemm(h, 'T', 'N', 'F', M, M, M, 1.0, Lw, ldlw, Y, ldy, 0.0, T, M, eng));  // Y = R^T Z
+    GEP_CHECK(copy_matrix(h, M, M, T, M, Y, ldy));
+  }
+  mark(h, o, 6);
+  GEP_CHECK(sign_convention(h, M, M, Y, ldy));
+  h->timers_recorded = o->timers != 0;
+  return GEP_OK;
+}
+
+int gep_workspace_size_host(gep_handle_t h, int M, const gep_options* o, size_t* bytes) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (M < 0) return -2;
+  if (!o) return -3;
+  if (!bytes) return -4;
+  gep_options oo = *o;
+  oo.overwrite = 1;
+  size_t mm = (size_t)M * M * sizeof(double);
+  *bytes = layout(M, &oo).end + 3 * r256(mm) + r256((size_t)(M + 1) * sizeof(double));
+  return GEP_OK;
+}
+
+int gep_solve_host(gep_handle_t h, int M, const double* A, int lda, const double* B, int ldb, double* w,
+                   double* Y, int ldy, const gep_options* o) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (M < 0) return -2;
+  if (M > 0 && !A) return -3;
+  if (lda < (M > 1 ? M : 1)) return -4;
+  if (M > 0 && !B) return -5;
+  if (ldb < (M > 1 ? M : 1)) return -6;
+  if (M > 0 && !w) return -7;
+  if (!o) return -10;
+  if (o->want_vectors && M > 0 && !Y) return -8;
+  if (o->want_vectors && ldy < (M > 1 ? M : 1)) return -9;
+  GEP_CHECK(check_opts(o));
+  if (M == 0) return GEP_OK;
+  size_t need = 0;
+  GEP_CHECK(gep_workspace_size_host(h, M, o, &need));
+  if (h->ws == nullptr || h->ws_bytes < need) return GEP_ERR_ALLOC;
+  gep_options oo = *o;
+  oo.overwrite = 1;
+  size_t mm = (size_t)M * M * sizeof(double);
+  size_t inner = layout(M, &oo).end;
+  char* base = h->ws;
+  double* dA = (double*)(base + inner);
+  double* dB = (double*)(base + inner + r256(mm));
+  double* dY = (double*)(base + inner + 2 * r256(mm));
+  double* dw = (double*)(base + inner + 3 * r256(mm));
+  cudaStream_t s = h->stream;
+  GEP_CUDA(cudaMemcpy2DAsync(dA, (size_t)M * sizeof(double), A, (size_t)lda * sizeof(double), (size_t)M * sizeof(double),
+                             M, cudaMemcpyHostToDevice, s));
+  GEP_CUDA(cudaMemcpy2DAsync(dB, (size_t)M * sizeof(double), B, (size_t)ldb * sizeof(double), (size_t)M * sizeof(double),
+                             M, cudaMemcpyHostToDevice, s));
+  // the inner solve must not see the H2D buffers as workspace
+  char* saved_ws = h->ws;
+  size_t saved_b = h->ws_bytes;
+  h->ws_bytes = inner;
+  int rc = gep_solve(h, M, dA, M, dB, M, dw, dY, M, &oo);
+  h->ws = saved_ws;
+  h->ws_bytes = saved_b;
+  if (rc != GEP_OK) return rc;
+  GEP_CUDA(cudaMemcpyAsync(w, dw, (size_t)M * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (o->want_vectors)
+    GEP_CUDA(cudaMemcpy2DAsync(Y, (size_t)ldy * sizeof(double), dY, (size_t)M * sizeof(double), (size_t)M * sizeof(double),
+                               M, cudaMemcpyDeviceToHost, s));
+  GEP_CUDA(cudaStreamSynchronize(s));
+  return GEP_OK;
+}
+
+}  // extern "C"

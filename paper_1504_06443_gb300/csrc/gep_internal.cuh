@@ -1,0 +1,125 @@
+// Internal declarations shared by the solver's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "gep.h"
+
+#define GEP_IX(i, j, ld) ((size_t)(i) + (size_t)(j) * (size_t)(ld))
+
+struct gep_handle_s {
+  cudaStream_t stream = nullptr;
+  int* d_status = nullptr;   // [0] numerical info, [1] error code (timeouts etc.)
+  char* ws = nullptr;        // caller workspace
+  size_t ws_bytes = 0;
+  long long launches = 0;
+  int sm_count = 152;
+  int magic = 0x6e70;
+  cudaEvent_t ev[8] = {};
+  bool timers_recorded = false;
+};
+
+namespace gep {
+
+// Bump allocator over the caller's workspace.
+struct Arena {
+  char* base;
+  size_t cap, off = 0;
+  bool ok = true;
+  Arena(void* b, size_t c) : base((char*)b), cap(c) {}
+  template <class T>
+  T* take(size_t n) {
+    size_t a = (off + 255) & ~(size_t)255;
+    size_t need = a + n * sizeof(T);
+    if (need > cap || base == nullptr) { ok = false; off = need; return nullptr; }
+    off = need;
+    return (T*)(base + a);
+  }
+};
+
+// Counting-only arena: used by workspace queries to size the same carving.
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+inline int check_launch(gep_handle_t h) {
+  h->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    fprintf(stderr, "gep: kernel launch failed: %s\n", cudaGetErrorString(e));
+    return GEP_ERR_CUDA;
+  }
+  return GEP_OK;
+}
+
+#define GEP_CHECK(x)                        \
+  do {                                      \
+    int _r = (x);                           \
+    if (_r != GEP_OK) return _r;            \
+  } while (0)
+
+#define GEP_CUDA(x)                                                                  \
+  do {                                                                               \
+    cudaError_t _e = (x);                                                            \
+    if (_e != cudaSuccess) {                                                         \
+      fprintf(stderr, "gep: %s failed: %s (%s:%d)\n", #x, cudaGetErrorString(_e), __FILE__, \
+              __LINE__);                                                             \
+      return GEP_ERR_CUDA;                                                           \
+    }                                                                                \
+  } while (0)
+
+// ---- dense contraction engines (gemm_f64.cu, gemm_oz.cu) ----
+// C = alpha op(A) op(B) + beta C; uplo 'L' restricts computation/storage to i >= j.
+int dgemm(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, double alpha,
+          const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
+          int engine);
+int dgemm_f64(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, double alpha,
+              const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc);
+int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, double alpha,
+             const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
+             int levels);
+size_t oz_workspace_bytes(int m, int n, int k);
+
+// ---- small dense helpers (blas_util.cu) ----
+int copy_matrix(gep_handle_t h, int m, int n, const double* src, int lds, double* dst, int ldd);
+int copy_lower(gep_handle_t h, int M, const double* src, int lds, double* dst, int ldd);
+int set_matrix(gep_handle_t h, int m, int n, double offdiag, double diag, double* A, int lda);
+int symmetrize_lower(gep_handle_t h, int M, double* A, int lda);  // upper := lower^T
+int transpose(gep_handle_t h, int m, int n, const double* src, int lds, double* dst, int ldd);
+int zero_upper(gep_handle_t h, int M, double* A, int lda);          // strict upper := 0
+int scan_nonfinite(gep_handle_t h, int M, const double* A, int lda);  // lower triangle
+
+// ---- triangular building blocks (tri.cu) ----
+// Inverts every nb x nb diagonal block of the lower triangular L into invD
+// (block b at invD + b*nb*nb, column-major nb x nb, lower; ragged last block padded
+// with identity).
+int tri_inv_diag_blocks(gep_handle_t h, int M, const double* L, int ldl, double* invD, int nb);
+// X (M x n) := L^-1 X  (left, lower, no transpose)
+int trsm_lln(gep_handle_t h, int M, int n, const double* L, int ldl, const double* invD, int nb,
+             double* X, int ldx, double* tmp, int engine);
+// X (M x n) := L^-T X  (left, lower, transpose)
+int trsm_llt(gep_handle_t h, int M, int n, const double* L, int ldl, const double* invD, int nb,
+             double* X, int ldx, double* tmp, int engine);
+size_t trsm_tmp_elems(int M, int n, int nb);
+
+// ---- stages ----
+int cholesky(gep_handle_t h, int M, double* B, int ldb, double* ws_invdiag, int engine);
+int reduce_twosided(gep_handle_t h, int M, double* A, int lda, const double* L, int ldl,
+                    const double* invD, double* X, double* tmp, int engine);
+int reduce_explicit_inv(gep_handle_t h, int M, double* A, int lda, double* L, int ldl,
+                        const double* invD, double* X, double* tmp, int engine);
+int tridiag_1stage(gep_handle_t h, int M, double* C, int ldc, double* d, double* e, double* tau,
+                   double* ws, size_t ws_elems, int engine);
+size_t tridiag_ws_elems(int M);
+int backtransform_q(gep_handle_t h, int M, int ncol, const double* C, int ldc, const double* tau,
+                    double* Z, int ldz, double* ws, size_t ws_elems, int engine);
+size_t backtransform_ws_elems(int M, int ncol);
+int tridiag_eig_dc(gep_handle_t h, int M, const double* d, const double* e, double* w, double* Z,
+                   int ldz, double* ws, size_t ws_elems, int engine);
+size_t dc_ws_bytes(int M);
+int tridiag_eig_bisect(gep_handle_t h, int M, const double* d, const double* e, double* w);
+int sign_convention(gep_handle_t h, int M, int ncol, double* Y, int ldy);
+
+// Kernel-side helper: returns true when an earlier stage recorded an error.
+__device__ __forceinline__ bool status_bad(const int* st) { return st != nullptr && (st[0] != 0 || st[1] != 0); }
+
+}  // namespace gep

@@ -1,0 +1,223 @@
+// Reducer stages (section 3.1 (b)):
+//   Eq. 4  B = L L^T              blocked right-looking Cholesky
+//   Eq. 5  C = L^-1 A L^-T         "ScaLAPACK style" (triangular solves, L^-1 never formed)
+//                                  "ELPA style" (R = L^-1 formed, then C = R A R^T)
+//   Eq. 6  Y = L^-T Z              blocked back-substitution
+// plus the triangular building blocks they share.  Every nb x nb diagonal block
+// of L is factored and inverted by one CTA in shared memory; everything else is
+// a dense product on the GEMM engine, so the O(M^3) work runs as matrix products.
+#include <math.h>
+
+#include "gep_internal.cuh"
+
+namespace gep {
+namespace {
+
+constexpr int NB = 128;  // diagonal block order
+
+// In-place inverse of the r x r lower triangular S (shared, leading dim NB),
+// from the bottom-right: column j of L^-1 is -(1/l_jj) * L22^-1 * l(j+1:, j).
+__device__ void tri_inv_smem(double* S, double* tmp, int r) {
+  for (int j = r - 1; j >= 0; --j) {
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < r; i += blockDim.x) {
+      double s = 0.0;
+      for (int q = j + 1; q <= i; ++q) s = fma(S[i + q * NB], S[q + j * NB], s);
+      tmp[i] = s;
+    }
+    __syncthreads();
+    double ajj = 1.0 / S[j + j * NB];
+    for (int i = j + 1 + threadIdx.x; i < r; i += blockDim.x) S[i + j * NB] = -ajj * tmp[i];
+    if (threadIdx.x == 0) S[j + j * NB] = ajj;
+  }
+  __syncthreads();
+}
+
+// Writes the r x r lower inverse from shared memory into an NB x NB block (identity
+// padding for r < NB, zero strict upper triangle).
+__device__ void store_inv(const double* S, int r, double* out) {
+  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+    int i = idx % NB, j = idx / NB;
+    double v;
+    if (i < r && j < r) v = (i >= j) ? S[i + j * NB] : 0.0;
+    else v = (i == j) ? 1.0 : 0.0;
+    out[idx] = v;
+  }
+}
+
+// Factor the diagonal block B(kb:kb+r, kb:kb+r) (already updated by earlier trailing
+// products) and store L_kk in place plus L_kk^-1 into invD.
+__global__ void __launch_bounds__(256) k_potrf_diag(int r, double* B, int ldb, double* invD, int kb,
+                                                    int* st) {
+  extern __shared__ double sm[];
+  double* S = sm;
+  double* tmp = sm + NB * NB;
+  __shared__ int fail;
+  if (status_bad(st)) return;
+  if (threadIdx.x == 0) fail = 0;
+  for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
+    int i = idx % r, j = idx / r;
+    S[i + j * NB] = (i >= j) ? B[GEP_IX(i, j, ldb)] : 0.0;
+  }
+  for (int j = 0; j < r; ++j) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double p = S[j + j * NB];
+      if (!(p > 0.0) || !isfinite(p)) fail = j + 1;
+      else S[j + j * NB] = sqrt(p);
+    }
+    __syncthreads();
+    if (fail) break;
+    double ljj = S[j + j * NB];
+    for (int i = j + 1 + threadIdx.x; i < r; i += blockDim.x) S[i + j * NB] /= ljj;
+    __syncthreads();
+    int w = r - j - 1;
+    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+      int ii = j + 1 + t % w, cc = j + 1 + t / w;
+      if (ii >= cc) S[ii + cc * NB] = fma(-S[ii + j * NB], S[cc + j * NB], S[ii + cc * NB]);
+    }
+  }
+  __syncthreads();
+  if (fail) {
+    if (threadIdx.x == 0) atomicCAS(st, 0, kb + fail);
+    return;
+  }
+  for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
+    int i = idx % r, j = idx / r;
+    if (i >= j) B[GEP_IX(i, j, ldb)] = S[i + j * NB];
+  }
+  tri_inv_smem(S, tmp, r);
+  store_inv(S, r, invD);
+}
+
+// One CTA per diagonal block of an existing lower triangular L: invert it.
+__global__ void __launch_bounds__(256) k_inv_diag(int M, const double* L, int ldl, double* invD,
+                                                  const int* st) {
+  extern __shared__ double sm[];
+  if (status_bad(st)) return;
+  double* S = sm;
+  double* tmp = sm + NB * NB;
+  int b = blockIdx.x, kb = b * NB;
+  int r = min(NB, M - kb);
+  for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
+    int i = idx % r, j = idx / r;
+    S[i + j * NB] = (i >= j) ? L[GEP_IX(kb + i, kb + j, ldl)] : 0.0;
+  }
+  tri_inv_smem(S, tmp, r);
+  store_inv(S, r, invD + (size_t)b * NB * NB);
+}
+
+constexpr size_t kSmemDiag = (size_t)NB * NB * sizeof(double) + NB * sizeof(double);
+
+int set_smem_attr() {
+  static int done = 0;
+  if (!done) {
+    cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDiag);
+    cudaFuncSetAttribute(k_inv_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDiag);
+    done = 1;
+  }
+  return GEP_OK;
+}
+
+}  // namespace
+
+size_t trsm_tmp_elems(int M, int n, int nb) { (void)M; return (size_t)nb * (size_t)(n > 0 ? n : 1); }
+
+int tri_inv_diag_blocks(gep_handle_t h, int M, const double* L, int ldl, double* invD, int nb) {
+  if (nb != NB) return GEP_ERR_UNSUPPORTED;
+  if (M <= 0) return GEP_OK;
+  set_smem_attr();
+  int nblk = (M + NB - 1) / NB;
+  k_inv_diag<<<nblk, 256, kSmemDiag, h->stream>>>(M, L, ldl, invD, h->d_status);
+  return check_launch(h);
+}
+
+// X := L^-1 X, blocked forward substitution; tmp holds NB x n.
+int trsm_lln(gep_handle_t h, int M, int n, const double* L, int ldl, const double* invD, int nb,
+             double* X, int ldx, double* tmp, int engine) {
+  if (nb != NB) return GEP_ERR_UNSUPPORTED;
+  for (int kb = 0; kb < M; kb += NB) {
+    int r = min(NB, M - kb);
+    const double* Dk = invD + (size_t)(kb / NB) * NB * NB;
+    GEP_CHECK(dgemm(h, 'N', 'N', 'F', r, n, r, 1.0, Dk, NB, X + kb, ldx, 0.0, tmp, r, engine));
+    GEP_CHECK(copy_matrix(h, r, n, tmp, r, X + kb, ldx));
+    int m2 = M - kb - r;
+    if (m2 > 0)
+      GEP_CHECK(dgemm(h, 'N', 'N', 'F', m2, n, r, -1.0, L + GEP_IX(kb + r, kb, ldl), ldl, X + kb, ldx,
+                      1.0, X + kb + r, ldx, engine));
+  }
+  return GEP_OK;
+}
+
+// X := L^-T X, blocked backward substitution with the upper triangular L^T.
+int trsm_llt(gep_handle_t h, int M, int n, const double* L, int ldl, const double* invD, int nb,
+             double* X, int ldx, double* tmp, int engine) {
+  if (nb != NB) return GEP_ERR_UNSUPPORTED;
+  int last = ((M - 1) / NB) * NB;
+  for (int kb = last; kb >= 0; kb -= NB) {
+    int r = min(NB, M - kb);
+    const double* Dk = invD + (size_t)(kb / NB) * NB * NB;
+    GEP_CHECK(dgemm(h, 'T', 'N', 'F', r, n, r, 1.0, Dk, NB, X + kb, ldx, 0.0, tmp, r, engine));
+    GEP_CHECK(copy_matrix(h, r, n, tmp, r, X + kb, ldx));
+    if (kb > 0)
+      GEP_CHECK(dgemm(h, 'T', 'N', 'F', kb, n, r, -1.0, L + kb, ldl, X + kb, ldx, 1.0, X, ldx, engine));
+  }
+  return GEP_OK;
+}
+
+// Eq. 4: blocked right-looking Cholesky.  invD receives the inverses of the
+// diagonal blocks (reused by the reduction and the back-substitution).  tmp must
+// hold M x NB doubles and follows invD in the caller's workspace.
+int cholesky(gep_handle_t h, int M, double* B, int ldb, double* invD, int engine) {
+  if (M <= 0) return GEP_OK;
+  set_smem_attr();
+  int nblk = (M + NB - 1) / NB;
+  double* tmp = invD + (size_t)nblk * NB * NB;
+  for (int kb = 0; kb < M; kb += NB) {
+    int r = min(NB, M - kb);
+    double* Dk = invD + (size_t)(kb / NB) * NB * NB;
+    k_potrf_diag<<<1, 256, kSmemDiag, h->stream>>>(r, B + GEP_IX(kb, kb, ldb), ldb, Dk, kb, h->d_status);
+    GEP_CHECK(check_launch(h));
+    int n2 = M - kb - r;
+    if (n2 <= 0) break;
+    double* P = B + GEP_IX(kb + r, kb, ldb);
+    // L21 = B21 L11^-T
+    GEP_CHECK(dgemm(h, 'N', 'T', 'F', n2, r, r, 1.0, P, ldb, Dk, NB, 0.0, tmp, n2, engine));
+    GEP_CHECK(copy_matrix(h, n2, r, tmp, n2, P, ldb));
+    // B22 -= L21 L21^T (lower triangle)
+    GEP_CHECK(dgemm(h, 'N', 'T', 'L', n2, n2, r, -1.0, P, ldb, P, ldb, 1.0,
+                    B + GEP_IX(kb + r, kb + r, ldb), ldb, engine));
+  }
+  return GEP_OK;
+}
+
+// Eq. 5, "ScaLAPACK style": C = L^-1 (L^-1 A)^T with two blocked triangular solves.
+// A (lower) is overwritten by the full symmetric C; X is an M x M scratch matrix.
+int reduce_twosided(gep_handle_t h, int M, double* A, int lda, const double* L, int ldl,
+                    const double* invD, double* X, double* tmp, int engine) {
+  if (M <= 0) return GEP_OK;
+  GEP_CHECK(symmetrize_lower(h, M, A, lda));
+  GEP_CHECK(trsm_lln(h, M, M, L, ldl, invD, NB, A, lda, tmp, engine));   // A := L^-1 A
+  GEP_CHECK(transpose(h, M, M, A, lda, X, M));                           // X := A L^-T
+  GEP_CHECK(trsm_lln(h, M, M, L, ldl, invD, NB, X, M, tmp, engine));     // X := L^-1 A L^-T
+  GEP_CHECK(copy_matrix(h, M, M, X, M, A, lda));
+  return symmetrize_lower(h, M, A, lda);
+}
+
+// Eq. 5, "ELPA style": R = L^-1 formed explicitly (R2), then C = (R A) R^T (R3, R4).
+// L (lower of B) is overwritten by R.  X and T are M x M scratch matrices (T = tmp2).
+int reduce_explicit_inv(gep_handle_t h, int M, double* A, int lda, double* L, int ldl,
+                        const double* invD, double* X, double* tmp, int engine) {
+  if (M <= 0) return GEP_OK;
+  double* T = tmp;                    // M x M
+  double* tmp_small = tmp + (size_t)M * M;  // NB x M
+  GEP_CHECK(set_matrix(h, M, M, 0.0, 1.0, X, M));
+  GEP_CHECK(trsm_lln(h, M, M, L, ldl, invD, NB, X, M, tmp_small, engine));  // X = R = L^-1
+  GEP_CHECK(symmetrize_lower(h, M, A, lda));
+  GEP_CHECK(dgemm(h, 'N', 'N', 'F', M, M, M, 1.0, X, M, A, lda, 0.0, T, M, engine));   // T = R A
+  GEP_CHECK(dgemm(h, 'N', 'T', 'L', M, M, M, 1.0, T, M, X, M, 0.0, A, lda, engine));   // C = T R^T
+  GEP_CHECK(symmetrize_lower(h, M, A, lda));
+  return copy_lower(h, M, X, M, L, ldl);  // lower(B) <- R
+}
+
+}  // namespace gep

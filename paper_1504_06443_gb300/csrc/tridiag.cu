@@ -1,0 +1,348 @@
+// SEP solver, stage "TRD" (Table 3): one-stage Householder reduction of the
+// symmetric C to tridiagonal form, C = Q T Q^T, Q = H_0 H_1 ... H_{M-2}.
+//
+// Blocked in panels of NBT columns (the conventional algorithm of the
+// ScaLAPACK/ELPA1/EigenExa "eigen_s" solvers of section 3.1).  Inside a panel,
+// column c needs one symmetric matrix-vector product with the trailing matrix
+// as it stood before the panel, corrected by the panel's earlier reflectors
+// (V) and their companions (W):  A_cur v = A v - V (W^T v) - W (V^T v).  After
+// the panel, the trailing matrix takes the rank-2*NBT update A -= V W^T + W V^T
+// on the GEMM engine.  Half of the flops are in the memory-bound SYMVs.
+//
+// The SYMV reads only the lower triangle (each 64-wide column strip once) and
+// is deterministic: every strip writes its partial sums to its own slots, and a
+// second kernel adds them in a fixed order.
+#include <math.h>
+
+#include "gep_internal.cuh"
+
+namespace gep {
+namespace {
+
+constexpr int NBT = 64;     // panel width
+constexpr int SW = 64;      // SYMV strip width
+constexpr int SCH = 1024;   // SYMV rows per CTA
+constexpr int DCH = 2048;   // panel dot-product rows per CTA
+
+struct TWs {
+  double *Vp, *W, *y, *Pd, *Pt, *part, *part2;
+  int M, nblk, maxch, ndch;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; every thread gets the result.  red must hold 32 doubles.
+__device__ double block_sum(double v, double* red) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+  if (w == 0) s = warp_sum(s);
+  if (threadIdx.x == 0) red[0] = s;
+  __syncthreads();
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Column c of the panel: C(r, c) -= sum_q V(r,q) W(c,q) + W(r,q) V(c,q), r >= c.
+__global__ void k_col_update(int M, int c, int i, double* C, int ldc, const double* __restrict__ Vp,
+                             const double* __restrict__ W, int ldp, const int* st) {
+  __shared__ double vc[NBT], wc[NBT];
+  if (status_bad(st)) return;
+  if (threadIdx.x < i) {
+    vc[threadIdx.x] = Vp[GEP_IX(c, threadIdx.x, ldp)];
+    wc[threadIdx.x] = W[GEP_IX(c, threadIdx.x, ldp)];
+  }
+  __syncthreads();
+  int r = c + blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= M) return;
+  double s = 0.0;
+  for (int q = 0; q < i; ++q) s = fma(Vp[GEP_IX(r, q, ldp)], wc[q], fma(W[GEP_IX(r, q, ldp)], vc[q], s));
+  C[GEP_IX(r, c, ldc)] -= s;
+}
+
+// Householder reflector of x = C(c+1:M, c):  H x = beta e_1, H = I - tau v v^T, v(0) = 1.
+// Writes d[c], e[c], tau[c], the reflector into C below the subdiagonal, and the
+// explicit column i of the panel V (zeros above row c+1).
+__global__ void __launch_bounds__(1024) k_householder(int M, int c, int i, double* C, int ldc, double* d,
+                                                      double* e, double* tau, double* Vp, int ldp,
+                                                      const int* st) {
+  __shared__ double red[32];
+  if (status_bad(st)) return;
+  int n = M - c - 1;
+  double* x = C + GEP_IX(c + 1, c, ldc);
+  double s = 0.0;
+  for (int t = 1 + threadIdx.x; t < n; t += blockDim.x) s = fma(x[t], x[t], s);
+  double sig = block_sum(s, red);
+  double alpha = x[0];
+  double beta, tv, scal;
+  if (sig == 0.0) {
+    tv = 0.0; beta = alpha; scal = 0.0;
+  } else {
+    double nrm = sqrt(alpha * alpha + sig);
+    beta = alpha >= 0.0 ? -nrm : nrm;
+    tv = (beta - alpha) / beta;
+    scal = 1.0 / (alpha - beta);
+  }
+  double* v = Vp + (size_t)i * ldp;
+  for (int r = threadIdx.x; r <= c; r += blockDim.x) v[r] = 0.0;
+  for (int t = 1 + threadIdx.x; t < n; t += blockDim.x) {
+    double vt = (sig == 0.0) ? 0.0 : x[t] * scal;
+    x[t] = vt;
+    v[c + 1 + t] = vt;
+  }
+  if (threadIdx.x == 0) {
+    d[c] = C[GEP_IX(c, c, ldc)];
+    e[c] = beta;
+    tau[c] = tv;
+    x[0] = beta;
+    v[c + 1] = 1.0;
+  }
+}
+
+__global__ void k_last_diag(int M, const double* C, int ldc, double* d, const int* st) {
+  if (status_bad(st)) return;
+  d[M - 1] = C[GEP_IX(M - 1, M - 1, ldc)];
+}
+
+// Partial products of the symmetric SYMV y = A v over strip jb (columns 64 jb ..),
+// rows [R0, R0 + SCH) of the lower triangle.  256 threads = 64 row lanes x 4 column
+// quarters of 16 columns.  Direct terms A(r,c) v(c) (r >= c) go to Pd[jb][r];
+// transposed terms A(r,c) v(r) (r > c) are summed per column into Pt[jb][ch][.].
+__global__ void __launch_bounds__(256) k_symv_partial(int n, const double* __restrict__ A, int lda,
+                                                      const double* __restrict__ v, double* __restrict__ Pd,
+                                                      double* __restrict__ Pt, int maxch, const int* st) {
+  __shared__ double vs[SW];
+  __shared__ double dsum[4][SCH];
+  __shared__ double tsum[4][2][16];
+  if (status_bad(st)) return;
+  int jb = blockIdx.x, ch = blockIdx.y;
+  int c0 = jb * SW;
+  int R0 = c0 + ch * SCH;
+  if (R0 >= n) return;
+  int rl = threadIdx.x & 63, cq = threadIdx.x >> 6;
+  if (threadIdx.x < SW) vs[threadIdx.x] = (c0 + threadIdx.x < n) ? v[c0 + threadIdx.x] : 0.0;
+  __syncthreads();
+  int cbase = c0 + cq * 16;
+  int ncols = min(16, n - cbase);  // may be <= 0 at the ragged end
+  double acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+  int rend = min(n, R0 + SCH);
+  for (int p = 0; p < SCH / 64; ++p) {
+    int r = R0 + p * 64 + rl;
+    double dir = 0.0;
+    if (r < rend && ncols > 0) {
+      double vr = v[r];
+      const double* arow = A + r;
+      if (r >= cbase + 16) {  // strictly below every column of this quarter
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          if (q < ncols) {
+            double a = arow[(size_t)(cbase + q) * lda];
+            dir = fma(a, vs[cq * 16 + q], dir);
+            acc[q] = fma(a, vr, acc[q]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          int col = cbase + q;
+          if (q < ncols && r >= col) {
+            double a = arow[(size_t)col * lda];
+            dir = fma(a, vs[cq * 16 + q], dir);
+            if (r > col) acc[q] = fma(a, vr, acc[q]);
+          }
+        }
+      }
+    }
+    dsum[cq][p * 64 + rl] = dir;
+  }
+  // transposed terms: reduce over the 64 row lanes (2 warps per quarter)
+  int lane = threadIdx.x & 31, wq = (threadIdx.x >> 5) & 1;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    double s = warp_sum(acc[q]);
+    if (lane == 0) tsum[cq][wq][q] = s;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < SCH; t += blockDim.x) {
+    int r = R0 + t;
+    if (r < rend) Pd[(size_t)jb * n + r] = (dsum[0][t] + dsum[1][t]) + (dsum[2][t] + dsum[3][t]);
+  }
+  if (threadIdx.x < SW) {
+    int q4 = threadIdx.x >> 4, q = threadIdx.x & 15;
+    Pt[((size_t)jb * maxch + ch) * SW + threadIdx.x] = tsum[q4][0][q] + tsum[q4][1][q];
+  }
+}
+
+// y(r) = sum_{jb <= r/64} Pd[jb][r] + sum_ch Pt[r/64][ch][r%64]
+__global__ void k_symv_reduce(int n, const double* __restrict__ Pd, const double* __restrict__ Pt, int maxch,
+                              double* __restrict__ y, const int* st) {
+  if (status_bad(st)) return;
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int jr = r / SW;
+  double s = 0.0;
+  for (int jb = 0; jb <= jr; ++jb) s += Pd[(size_t)jb * n + r];
+  int nch = (n - jr * SW + SCH - 1) / SCH;
+  double t = 0.0;
+  for (int ch = 0; ch < nch; ++ch) t += Pt[((size_t)jr * maxch + ch) * SW + (r - jr * SW)];
+  y[r] = s + t;
+}
+
+// Partial dots over rows [ch*DCH, ...) of t1 = W(:,0:i)^T v and t2 = V(:,0:i)^T v
+// (rows c+1 .. M-1 of the panel).  One warp per (matrix, column).
+__global__ void __launch_bounds__(256) k_panel_dots(int n, int i, const double* __restrict__ Vp,
+                                                    const double* __restrict__ W, int ldp,
+                                                    const double* __restrict__ v, double* __restrict__ part,
+                                                    const int* st) {
+  if (status_bad(st)) return;
+  int ch = blockIdx.x;
+  int r0 = ch * DCH, r1 = min(n, r0 + DCH);
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int q = warp; q < 2 * i; q += 8) {
+    const double* col = (q < i) ? (W + (size_t)q * ldp) : (Vp + (size_t)(q - i) * ldp);
+    double s = 0.0;
+    for (int r = r0 + lane; r < r1; r += 32) s = fma(col[r], v[r], s);
+    s = warp_sum(s);
+    if (lane == 0) part[(size_t)ch * 2 * NBT + q] = s;
+  }
+}
+
+// w = tau (y - V t1 - W t2) on rows [blk*256, ...); also writes partial w.v.
+__global__ void __launch_bounds__(256) k_w_compute(int n, int i, int nch, const double* __restrict__ Vp,
+                                                   const double* __restrict__ W, int ldp,
+                                                   const double* __restrict__ v, double* __restrict__ y,
+                                                   const double* __restrict__ part, const double* tau_c,
+                                                   double* __restrict__ part2, const int* st) {
+  __shared__ double t[2 * NBT];
+  __shared__ double red[32];
+  if (status_bad(st)) return;
+  if (threadIdx.x < 2 * i) {
+    double s = 0.0;
+    for (int ch = 0; ch < nch; ++ch) s += part[(size_t)ch * 2 * NBT + threadIdx.x];
+    t[threadIdx.x] = s;
+  }
+  __syncthreads();
+  double tv = *tau_c;
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  double dotp = 0.0;
+  if (r < n) {
+    double s = y[r];
+    for (int q = 0; q < i; ++q) s -= Vp[GEP_IX(r, q, ldp)] * t[q] + W[GEP_IX(r, q, ldp)] * t[i + q];
+    double w = tv * s;
+    y[r] = w;
+    dotp = w * v[r];
+  }
+  double tot = block_sum(dotp, red);
+  if (threadIdx.x == 0) part2[blockIdx.x] = tot;
+}
+
+// alpha = -tau/2 (w.v);  W(:, i) = w + alpha v  (rows c+1 ..).
+__global__ void __launch_bounds__(256) k_w_finish(int n, int nblk, const double* __restrict__ y,
+                                                  const double* __restrict__ v, const double* __restrict__ part2,
+                                                  const double* tau_c, double* __restrict__ Wi, const int* st) {
+  __shared__ double red[32];
+  if (status_bad(st)) return;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part2[b];
+  double dot = block_sum(s, red);
+  double alpha = -0.5 * (*tau_c) * dot;
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) Wi[r] = fma(alpha, v[r], y[r]);
+}
+
+TWs carve(double* ws, int M) {
+  TWs t;
+  t.M = M;
+  t.nblk = (M + SW - 1) / SW;
+  t.maxch = (M + SCH - 1) / SCH;
+  t.ndch = (M + DCH - 1) / DCH;
+  size_t o = 0;
+  auto take = [&](size_t n) { double* p = ws + o; o += (n + 31) & ~(size_t)31; return p; };
+  t.Vp = take((size_t)M * NBT);
+  t.W = take((size_t)M * NBT);
+  t.y = take((size_t)M);
+  t.Pd = take((size_t)t.nblk * M);
+  t.Pt = take((size_t)t.nblk * t.maxch * SW);
+  t.part = take((size_t)t.ndch * 2 * NBT);
+  t.part2 = take((size_t)(M + 255) / 256 + 1);
+  return t;
+}
+
+}  // namespace
+
+size_t tridiag_ws_elems(int M) {
+  size_t nblk = (M + SW - 1) / SW, maxch = (M + SCH - 1) / SCH, ndch = (M + DCH - 1) / DCH;
+  auto r = [](size_t n) { return (n + 31) & ~(size_t)31; };
+  return r((size_t)M * NBT) * 2 + r(M) + r(nblk * M) + r(nblk * maxch * SW) + r(ndch * 2 * NBT) +
+         r((M + 255) / 256 + 1);
+}
+
+int tridiag_1stage(gep_handle_t h, int M, double* C, int ldc, double* d, double* e, double* tau,
+                   double* ws, size_t ws_elems, int engine) {
+  if (M <= 0) return GEP_OK;
+  if (ws_elems < tridiag_ws_elems(M)) return GEP_ERR_ALLOC;
+  TWs t = carve(ws, M);
+  const int ldp = M;
+  cudaStream_t s = h->stream;
+  const int* st = h->d_status;
+  for (int j0 = 0; j0 < M; j0 += NBT) {
+    int nbp = min(NBT, M - j0);
+    int done = 0;
+    for (int i = 0; i < nbp; ++i) {
+      int c = j0 + i;
+      if (i > 0) {
+        k_col_update<<<(M - c + 255) / 256, 256, 0, s>>>(M, c, i, C, ldc, t.Vp + j0 * 0, t.W, ldp, st);
+        GEP_CHECK(check_launch(h));
+      }
+      if (c == M - 1) {
+        k_last_diag<<<1, 1, 0, s>>>(M, C, ldc, d, st);
+        GEP_CHECK(check_launch(h));
+        done = 1;
+        break;
+      }
+      k_householder<<<1, 1024, 0, s>>>(M, c, i, C, ldc, d, e, tau, t.Vp, ldp, st);
+      GEP_CHECK(check_launch(h));
+      int n = M - c - 1;
+      const double* v = t.Vp + GEP_IX(c + 1, i, ldp);
+      const double* A = C + GEP_IX(c + 1, c + 1, ldc);
+      int nblk = (n + SW - 1) / SW, maxch = (n + SCH - 1) / SCH;
+      k_symv_partial<<<dim3(nblk, maxch), 256, 0, s>>>(n, A, ldc, v, t.Pd, t.Pt, maxch, st);
+      GEP_CHECK(check_launch(h));
+      k_symv_reduce<<<(n + 255) / 256, 256, 0, s>>>(n, t.Pd, t.Pt, maxch, t.y, st);
+      GEP_CHECK(check_launch(h));
+      int ndch = (n + DCH - 1) / DCH;
+      if (i > 0) {
+        k_panel_dots<<<ndch, 256, 0, s>>>(n, i, t.Vp + (c + 1), t.W + (c + 1), ldp, v, t.part, st);
+        GEP_CHECK(check_launch(h));
+      }
+      int nb256 = (n + 255) / 256;
+      k_w_compute<<<nb256, 256, 0, s>>>(n, i, ndch, t.Vp + (c + 1), t.W + (c + 1), ldp, v, t.y, t.part,
+                                        tau + c, t.part2, st);
+      GEP_CHECK(check_launch(h));
+      k_w_finish<<<nb256, 256, 0, s>>>(n, nb256, t.y, v, t.part2, tau + c, t.W + GEP_IX(c + 1, i, ldp), st);
+      GEP_CHECK(check_launch(h));
+    }
+    if (done) break;
+    int jn = j0 + nbp;
+    int n2 = M - jn;
+    if (n2 > 0) {
+      // A(jn:, jn:) -= V W^T + W V^T on the lower triangle
+      GEP_CHECK(dgemm(h, 'N', 'T', 'L', n2, n2, nbp, -1.0, t.Vp + jn, ldp, t.W + jn, ldp, 1.0,
+                      C + GEP_IX(jn, jn, ldc), ldc, engine));
+      GEP_CHECK(dgemm(h, 'N', 'T', 'L', n2, n2, nbp, -1.0, t.W + jn, ldp, t.Vp + jn, ldp, 1.0,
+                      C + GEP_IX(jn, jn, ldc), ldc, engine));
+    }
+  }
+  return GEP_OK;
+}
+
+}  // namespace gep

@@ -1,0 +1,63 @@
+"""CPU-side checks of the C-ABI boundary: the library builds, loads and exports
+every function declared in include/gep.h; the header is valid C."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gep.h")
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ ]*[\s\*]+([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if n.startswith(("gep_", "sep_"))))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1504_06443_gb300 import build
+    return build.build()
+
+
+def test_header_is_valid_c(tmp_path):
+    t = tmp_path / "inc.c"
+    t.write_text('#include "gep.h"\nint main(void){gep_options o; gep_default_options(&o); return o.sep;}\n')
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-c", str(t),
+                        "-o", str(tmp_path / "inc.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    names = _declared_functions()
+    assert len(names) >= 20, names
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_exports_are_c_linkage(libpath):
+    r = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True)
+    syms = set(line.split()[-1] for line in r.stdout.splitlines() if line.strip())
+    for n in _declared_functions():
+        assert n in syms, n
+
+
+def test_status_strings_without_gpu(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.gep_status_string.restype = ctypes.c_char_p
+    lib.gep_status_string.argtypes = [ctypes.c_int]
+    assert lib.gep_status_string(0) == b"ok"
+    assert b"illegal" in lib.gep_status_string(-3)
+    assert b"workspace" in lib.gep_status_string(-101)
+
+
+def test_null_handle_rejected_without_gpu(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.gep_cholesky.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+    lib.gep_cholesky.restype = ctypes.c_int
+    assert lib.gep_cholesky(None, 4, None, 4) == -104
