@@ -1,0 +1,314 @@
+#!/usr/bin/env python3
+"""Benchmark: all-eigenpair solve of the FP64 generalized eigenproblem A y = lambda B y
+at M = 32768 (tight-binding pencil, 8192 atoms x 4 sp orbitals) on one GB300.
+
+Contract (one JSON line on rank 0):
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+A step is one full solve (Cholesky, reduction, tridiagonalisation, divide and conquer,
+Householder back-transform, back-substitution) of a device-resident pencil;
+`value` is seconds per solve (max over ranks).  Under torchrun every rank solves its
+own pencil (replicas; the method has no exchange step).  --impl reference times the
+FP64 CPU oracle on the machine's host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GEP solve time (all eigenpairs, FP64-accurate) at M=32768"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--M", type=int, default=32768)
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--precision", default="fp64_emulated", choices=["fp64_emulated", "fp64"])
+    p.add_argument("--reducer", default="twosided", choices=["twosided", "explicit_inv"])
+    p.add_argument("--cpu-sample-M", type=int, default=2048)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-check", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region."""
+
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_sample(M_s, seed):
+    """Oracle (FP64 CPU) full solve of an M_s tight-binding pencil; returns (seconds, cores)."""
+    import gep_inputs as gi
+    import oracle
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    oracle.build()
+    tb = gi.tight_binding(M_s, seed)
+    t0 = time.perf_counter()
+    _, _, info = oracle.gep_solve(tb["A"], tb["B"], want_vectors=True)
+    dt = time.perf_counter() - t0
+    return dt, int(os.environ.get("OMP_NUM_THREADS", cores)), info
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    M, Ms = a.M, a.cpu_sample_M
+    scale = (M / Ms) ** 3
+    for _ in range(a.warmup):
+        cpu_sample(Ms, a.seed)
+    ts = []
+    cores = None
+    for _ in range(a.steps):
+        dt, cores, info = cpu_sample(Ms, a.seed)
+        ts.append(dt)
+    v = sum(ts) / len(ts) * scale
+    sample = (f"oracle full GEP solve (all eigenpairs) of the M={Ms} tight-binding pencil ({Ms // 4} atoms), "
+              f"host time x (M/{Ms})^3 = x{scale:.0f}")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"tight-binding GEP M={M} ({M // 4} atoms x 4 sp orbitals), all eigenpairs",
+                       "M": M, "seed": a.seed, "sampled_M": Ms},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def sampled_check(A, B, w, Y, ncols=64, seed=0):
+    """Residual / B-orthogonality / Rayleigh-quotient checks on sampled eigenpairs
+    (plain torch FP64 on the GPU, independent of the solver library)."""
+    import torch
+    M = A.shape[0]
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    idx = torch.randperm(M, generator=g)[:ncols].sort().values.to(A.device)
+    Ys = Y[:, idx].contiguous()
+    AY = A @ Ys
+    BY = B @ Ys
+    ws = w[idx]
+    R = AY - BY * ws[None, :]
+    res = (R.norm(dim=0) / (A.norm() / math.sqrt(M))).max().item()  # per-column, scaled like ||A||_F / sqrt(M)
+    G = Ys.t() @ BY
+    orth = (G - torch.eye(ncols, dtype=G.dtype, device=G.device)).abs().max().item()
+    rq = ((Ys * AY).sum(0) / (Ys * BY).sum(0) - ws).abs().max().item()
+    return {"cols": ncols, "max_col_residual_over_normA_rms": res, "orth_max": orth, "rayleigh_minus_w_max": rq,
+            "ascending": bool((w[1:] >= w[:-1]).all().item())}
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(a, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    import gep_inputs as gi
+    from paper_1504_06443_gb300 import build as gbuild
+    import paper_1504_06443_gb300 as gep
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    gbuild.build()
+    M = a.M
+    seed = a.seed + rank
+    t0 = time.time()
+    tb = gi.tight_binding(M, seed)
+    gen_s = time.time() - t0
+    A = torch.as_tensor(tb["A"]).to("cuda")
+    B = torch.as_tensor(tb["B"]).to("cuda")
+    if a.no_e2e:
+        del tb
+    w = torch.empty(M, dtype=torch.float64, device="cuda")
+    Yt = torch.empty((M, M), dtype=torch.float64, device="cuda")
+    h = gep.default_handle()
+    opts = gep.make_options(reducer=a.reducer, precision=a.precision, timers=True)
+    h.ensure_workspace(gep.workspace_bytes(M, handle=h, reducer=a.reducer, precision=a.precision, timers=True))
+    stream = torch.cuda.current_stream()
+
+    for _ in range(a.warmup):
+        gep.solve_async(A, B, w, Yt, opts, h)
+    torch.cuda.synchronize()
+    info = h.info()
+    h.launches(reset=True)
+    h.profile_enable(65536)
+    clk = Clocks(local)
+    clk.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        gep.solve_async(A, B, w, Yt, opts, h)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    launches = h.launches(reset=True) / a.steps
+    prof = h.profile_read(reset=True)
+    h.profile_enable(0)
+    stages = h.stage_times()
+    info = max(info, h.info())
+    t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = t_local.item()
+
+    check = None
+    if not a.no_check:
+        check = sampled_check(A, B, w, Yt.t(), 64, seed)
+
+    e2e = None
+    if not a.no_e2e:
+        Ah = torch.from_numpy(tb["A"]).pin_memory()
+        Bh = torch.from_numpy(tb["B"]).pin_memory()
+        del tb
+        wh = torch.empty(M, dtype=torch.float64).pin_memory()
+        Yh = torch.empty((M, M), dtype=torch.float64).pin_memory()
+        del Yt
+        torch.cuda.empty_cache()
+        hh = gep.Handle()
+        import ctypes
+        o = gep.make_options(reducer=a.reducer, precision=a.precision)
+        nb = ctypes.c_size_t()
+        hh.lib.gep_workspace_size_host(hh.h, M, ctypes.byref(o), ctypes.byref(nb))
+        h.ws = None
+        torch.cuda.empty_cache()
+        hh.ensure_workspace(nb.value)
+        P = ctypes.c_void_p
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        rc = hh.lib.gep_solve_host(hh.h, M, P(Ah.data_ptr()), M, P(Bh.data_ptr()), M, P(wh.data_ptr()),
+                                   P(Yh.data_ptr()), M, ctypes.byref(o))
+        e2e_s = time.perf_counter() - t1
+        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 2 * 8 * M * M, "d2h_bytes_per_step": 8 * M + 8 * M * M,
+               "rc": rc, "max_abs_dw_vs_device": float((wh.cuda() - w).abs().max().item())}
+
+    pk, pk_kind = peaks()
+    t_kernel_ms = prof["ms"] / a.steps if prof["launches"] else None
+    achieved = (prof["tensor_flops"] / (prof["ms"] * 1e-3) / 1e12) if prof["ms"] > 0 else None
+    peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    roof = {"bound": "tensor", "kernel": "k_oz_gemm (split-BF16 tcgen05 product)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "peak_kind": f"{pk_kind} bf16 dense sustained",
+            "fp64_equiv_tflops": (prof["fp64_flops"] / (prof["ms"] * 1e-3) / 1e12) if prof["ms"] > 0 else None,
+            "kernel_ms_per_step": t_kernel_ms, "timed_launches": prof["launches"], "untimed_launches": prof["skipped"],
+            "share_of_step": (t_kernel_ms / ms) if t_kernel_ms else None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        del A, B
+        torch.cuda.empty_cache()
+        dt, cores, cinfo = cpu_sample(a.cpu_sample_M, a.seed)
+        scale = (M / a.cpu_sample_M) ** 3
+        cpu = {"value": dt * scale, "unit": "s", "cores": cores, "kind": "oracle",
+               "sample": f"oracle full GEP solve of the M={a.cpu_sample_M} tight-binding pencil "
+                         f"({a.cpu_sample_M // 4} atoms) took {dt:.2f} s; scaled by (M/{a.cpu_sample_M})^3"}
+
+    flops_alg = (1.0 / 3 + 2.0 + 4.0 / 3 + 8.0 / 3 + 2.0 + 1.0) * float(M) ** 3
+    if rank == 0:
+        line = {"metric": METRIC, "value": ms_max / 1e3, "unit": "s", "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"tight-binding GEP M={M} ({M // 4} atoms x 4 sp orbitals), all eigenpairs",
+                           "M": M, "seed": a.seed, "reducer": a.reducer, "sep": "1stage",
+                           "precision": a.precision, "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "inputs larger than L2 (8.6 GB per matrix at M=32768)",
+                           "generator_s": round(gen_s, 2)},
+                "stage_ms": dict(zip(["R1_cholesky", "R2_reduce", "S1_tridiag", "S2_dc", "S3_back_q",
+                                      "R3_backsub"], [round(x, 2) for x in stages])),
+                "info": info, "gpu_launches": int(launches),
+                "fp64_equiv_tflops_whole_solve": flops_alg / (ms_max * 1e-3) / 1e12,
+                "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "check": check}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

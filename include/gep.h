@@ -147,6 +147,18 @@ int gep_get_stage_times(gep_handle_t h, double t[6]);
 /* Number of kernels the library launched since gep_create / last reset. */
 long long gep_launch_count(gep_handle_t h, int reset);
 
+/* Per-launch timing of the split-BF16 tensor-core product kernel (measurement aid;
+ * no counterpart in the paper).  gep_profile_enable(h, cap) records a CUDA event
+ * pair around each of the next `cap` launches (cap = 0 switches recording off and
+ * releases the events).  gep_profile_read synchronises the stream and returns the
+ * summed kernel time (ms), the tensor-core flops those launches performed (all
+ * digit-plane products), their FP64-equivalent flops (2mnk), the number of timed
+ * launches and of launches not timed because the pool was full; reset != 0 clears
+ * the counters. */
+int gep_profile_enable(gep_handle_t h, int cap);
+int gep_profile_read(gep_handle_t h, double* ms, double* tensor_flops, double* fp64_flops, long long* launches,
+                     long long* skipped, int reset);
+
 const char* gep_status_string(int code);
 
 /* ---- FP64 matrix product (the dense contraction every stage is built on) ------

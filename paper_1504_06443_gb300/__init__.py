@@ -89,6 +89,9 @@ def load():
             "gep_reset_info": (_I, [_P]),
             "gep_get_stage_times": (_I, [_P, ctypes.POINTER(_D)]),
             "gep_launch_count": (ctypes.c_longlong, [_P, _I]),
+            "gep_profile_enable": (_I, [_P, _I]),
+            "gep_profile_read": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D),
+                                      ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), _I]),
             "gep_status_string": (ctypes.c_char_p, [_I]),
             "gep_dgemm": (_I, [_P, ctypes.c_char, ctypes.c_char, ctypes.c_char, _I, _I, _I, _D, _P, _I, _P, _I,
                                _D, _P, _I, _I]),
@@ -187,6 +190,16 @@ class Handle:
 
     def launches(self, reset=False):
         return int(self.lib.gep_launch_count(self.h, 1 if reset else 0))
+
+    def profile_enable(self, cap):
+        _check(self.lib.gep_profile_enable(self.h, int(cap)), "gep_profile_enable")
+
+    def profile_read(self, reset=True):
+        ms, f, f64 = _D(), _D(), _D()
+        n, sk = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(self.lib.gep_profile_read(self.h, ctypes.byref(ms), ctypes.byref(f), ctypes.byref(f64), ctypes.byref(n),
+                                         ctypes.byref(sk), 1 if reset else 0), "gep_profile_read")
+        return dict(ms=ms.value, tensor_flops=f.value, fp64_flops=f64.value, launches=n.value, skipped=sk.value)
 
 
 _handles = {}
@@ -374,6 +387,8 @@ def dgemm(A, B, transa="N", transb="N", alpha=1.0, beta=0.0, C=None, uplo="F", e
     k = Ac.shape[0] if transa == "T" else Ac.shape[1]
     n = Bc.shape[0] if transb == "T" else Bc.shape[1]
     Cc = colmajor(C.clone()) if C is not None else torch.zeros((n, m), dtype=torch.float64, device=A.device).t()
+    kp = min(max(k, 1), 4096)
+    h.ensure_workspace(8 * (m + n) * (kp + 32) * 2 + 4 * (m + n) + 8192)
     _check(h.lib.gep_dgemm(h.h, transa.encode(), transb.encode(), uplo.encode(), m, n, k, float(alpha), _ptr(Ac),
                            _ld(Ac), _ptr(Bc), _ld(Bc), float(beta), _ptr(Cc), _ld(Cc), _PRECS[engine]), "gep_dgemm")
     return Cc

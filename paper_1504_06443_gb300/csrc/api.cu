@@ -15,8 +15,8 @@ constexpr int NB = 128;  // diagonal block order of the triangular kernels (tri.
 bool handle_ok(gep_handle_t h) { return h != nullptr && h->magic == 0x6e70; }
 
 struct SolveLayout {
-  size_t Cw, Lw, invD, vec, uni, end;  // byte offsets
-  size_t uni_bytes;
+  size_t Cw, Lw, invD, vec, uni, eng, end;  // byte offsets
+  size_t uni_bytes, eng_bytes;
 };
 
 size_t r256(size_t x) { return align256(x); }
@@ -53,6 +53,9 @@ SolveLayout layout(int M, const gep_options* o) {
   L.uni = off;
   L.uni_bytes = union_bytes(M, o);
   off += L.uni_bytes;
+  L.eng = off;
+  L.eng_bytes = (o->precision == GEP_PREC_FP64) ? 0 : r256(oz_workspace_bytes(M, M, M));
+  off += L.eng_bytes;
   L.end = off;
   return L;
 }
@@ -104,7 +107,7 @@ int gep_create(gep_handle_t* out, void* stream) {
 
 int gep_destroy(gep_handle_t h) {
   if (!handle_ok(h)) return GEP_ERR_HANDLE;
-  cudaStreamSynchronize(h->stream);
+  gep_profile_enable(h, 0);
   for (int i = 0; i < 8; ++i) cudaEventDestroy(h->ev[i]);
   cudaFree(h->d_status);
   h->magic = 0;
@@ -158,6 +161,55 @@ long long gep_launch_count(gep_handle_t h, int reset) {
   return n;
 }
 
+int gep_profile_enable(gep_handle_t h, int cap) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (cap < 0) return -2;
+  GEP_CUDA(cudaStreamSynchronize(h->stream));
+  if (h->prof_ev) {
+    for (int i = 0; i < 2 * h->prof_cap; ++i) cudaEventDestroy(h->prof_ev[i]);
+    delete[] h->prof_ev;
+    delete[] h->prof_flops;
+    delete[] h->prof_f64eq;
+    h->prof_ev = nullptr;
+    h->prof_flops = h->prof_f64eq = nullptr;
+  }
+  h->prof_on = 0;
+  h->prof_cap = h->prof_used = 0;
+  h->prof_skipped = 0;
+  if (cap == 0) return GEP_OK;
+  h->prof_ev = new cudaEvent_t[2 * (size_t)cap];
+  h->prof_flops = new double[cap];
+  h->prof_f64eq = new double[cap];
+  for (int i = 0; i < 2 * cap; ++i) GEP_CUDA(cudaEventCreate(&h->prof_ev[i]));
+  h->prof_cap = cap;
+  h->prof_on = 1;
+  return GEP_OK;
+}
+
+int gep_profile_read(gep_handle_t h, double* ms, double* tensor_flops, double* fp64_flops, long long* launches,
+                     long long* skipped, int reset) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  GEP_CUDA(cudaStreamSynchronize(h->stream));
+  double t = 0.0, f = 0.0, f64 = 0.0;
+  for (int i = 0; i < h->prof_used; ++i) {
+    float e = 0.f;
+    GEP_CUDA(cudaEventElapsedTime(&e, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]));
+    t += e;
+    f += h->prof_flops[i];
+    f64 += h->prof_f64eq[i];
+  }
+  if (ms) *ms = t;
+  if (tensor_flops) *tensor_flops = f;
+  if (fp64_flops) *fp64_flops = f64;
+  if (launches) *launches = h->prof_used;
+  if (skipped) *skipped = h->prof_skipped;
+  if (reset) {
+    h->prof_used = 0;
+    h->prof_skipped = 0;
+  }
+  return GEP_OK;
+}
+
 int gep_get_stage_times(gep_handle_t h, double t[6]) {
   if (!handle_ok(h)) return GEP_ERR_HANDLE;
   if (!t) return -2;
@@ -202,6 +254,8 @@ int gep_dgemm(gep_handle_t h, char transa, char transb, char uplo, int m, int n,
   if (ldb < (tb ? (n > 1 ? n : 1) : (k > 1 ? k : 1))) return -12;
   if (ldc < (m > 1 ? m : 1)) return -15;
   if (engine != GEP_PREC_FP64 && engine != GEP_PREC_FP64_EMULATED && engine != GEP_PREC_MIXED_REFINED) return -16;
+  h->eng_ws = h->ws;  // the whole caller workspace serves as product-engine scratch
+  h->eng_bytes = h->ws_bytes;
   return dgemm(h, transa, transb, uplo, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, engine);
 }
 
@@ -344,6 +398,8 @@ int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, dou
   double* evec = dvec + (M + 1);
   double* tvec = evec + (M + 1);
   char* uni = base + Ly.uni;
+  h->eng_ws = Ly.eng_bytes ? base + Ly.eng : nullptr;
+  h->eng_bytes = Ly.eng_bytes;
   h->timers_recorded = false;
 
   GEP_CHECK(reset_status(h));

@@ -78,9 +78,12 @@ int backtransform_q(gep_handle_t h, int M, int ncol, const double* C, int ldc, c
     k_larft<<<1, NBB, 0, h->stream>>>(nb, G, tau + j0, T, h->d_status);
     GEP_CHECK(check_launch(h));
     double* Zs = Z + (j0 + 1);
-    GEP_CHECK(dgemm(h, 'T', 'N', 'F', nb, ncol, rows, 1.0, V, rows, Zs, ldz, 0.0, W1, nb, engine));
-    GEP_CHECK(dgemm(h, 'N', 'N', 'F', nb, ncol, nb, 1.0, T, nb, W1, nb, 0.0, W2, nb, engine));
-    GEP_CHECK(dgemm(h, 'N', 'N', 'F', rows, ncol, nb, -1.0, V, rows, W2, nb, 1.0, Zs, ldz, engine));
+    // transposed products keep the long dimension (ncol) as the row dimension of
+    // each product, so all three fill full tensor-core tiles:
+    //   W1^T = Z^T V,  W2^T = W1^T T^T,  Z -= V W2 = V (W2^T)^T
+    GEP_CHECK(dgemm(h, 'T', 'N', 'F', ncol, nb, rows, 1.0, Zs, ldz, V, rows, 0.0, W1, ncol, engine));
+    GEP_CHECK(dgemm(h, 'N', 'T', 'F', ncol, nb, nb, 1.0, W1, ncol, T, nb, 0.0, W2, ncol, engine));
+    GEP_CHECK(dgemm(h, 'N', 'T', 'F', rows, ncol, nb, -1.0, V, rows, W2, ncol, 1.0, Zs, ldz, engine));
   }
   return GEP_OK;
 }

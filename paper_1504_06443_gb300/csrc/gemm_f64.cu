@@ -125,10 +125,12 @@ int dgemm_f64(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, 
 int dgemm(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, double alpha,
           const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
           int engine) {
-  if (engine == GEP_PREC_FP64_EMULATED)
+  // Products too small to fill 128 x 64 tensor-core tiles stay on the FP64 FMA kernel.
+  bool big = m >= 128 && n >= 64 && k >= 16;
+  if (engine == GEP_PREC_FP64_EMULATED && big)
     return dgemm_oz(h, ta, tb, uplo, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 9);
-  if (engine == GEP_PREC_MIXED_REFINED)
-    return dgemm_oz(h, ta, tb, uplo, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 3);
+  if (engine == GEP_PREC_MIXED_REFINED && big)
+    return dgemm_oz(h, ta, tb, uplo, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 4);
   return dgemm_f64(h, ta, tb, uplo, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 

@@ -1,16 +1,555 @@
-// FP64-accurate matrix product on the BF16 tensor cores (split-BF16 / Ozaki-style).
+// FP64-accurate matrix product C = alpha op(A) op(B) + beta C on the BF16 tensor
+// cores of sm_103a (tcgen05 + TMEM + TMA), by exact splitting of the operands.
+//
+// Splitting (per K panel): every row i of op(A) is scaled by 2^-e_i with
+// max_k |A_ik| < 2^e_i and cut into S signed 7-bit digits,
+//     A_ik 2^-e_i = sum_s d_s 2^-7s + r,   d_1 in [-128,128], d_s in [-64,64],
+// each digit an integer held exactly in BF16; likewise every column j of op(B)
+// with 2^-f_j.  Then
+//     (op(A) op(B))_ij = 2^(e_i+f_j) sum_l 2^-7l L_l,   L_l = sum_{s+t=l} D^A_s D^B_t,
+// and only levels l <= LMAX are kept.  With S = 8 planes and LMAX = 9 (36 plane
+// products, the FP64 setting) the dropped levels and the digit remainders sit
+// near 2^-55 of the row/column scale; S = 3, LMAX = 4 (6 products) is the
+// FP32-grade setting of the mixed-precision path.  Each L_l is an integer
+// matrix product: over a 256-deep K chunk every partial sum stays below 2^24 in
+// magnitude, so the FP32 accumulation in tensor memory is exact.  After each
+// chunk the level sums are drained from TMEM into two 64-bit integer fixed-point
+// accumulators per output (levels 2..4 and 5..LMAX); FP64 arithmetic appears only
+// once per output element, in the final epilogue.
+//
+// Kernel: one 128 x 64 output tile per CTA, 10 warps: warp 0 issues TMA loads of
+// all S digit planes of a 32-deep K step (3-D boxes, 64-byte swizzle) into a
+// two-stage ring; warp 1 issues tcgen05.mma (M=128, K=16, N up to 256 covering
+// several levels at once: for fixed s the planes B_1..B_{LMAX-s} are contiguous in
+// shared memory and their levels are contiguous TMEM columns); warps 2-9 drain
+// TMEM (warp w reads lane quarter w%4, column half (w-2)/4).  Every mbarrier wait
+// is bounded; on expiry the kernel records GEP_ERR_TIMEOUT in the status block,
+// waits (bounded) for its own copies and MMAs, frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <math.h>
+
 #include "gep_internal.cuh"
 
 namespace gep {
+namespace {
 
-size_t oz_workspace_bytes(int m, int n, int k) { (void)m; (void)n; (void)k; return 0; }
+constexpr int TM = 128, TN = 64, TK = 32, KCH = 256, STAGES = 2, MAXS = 8;
+constexpr int NTHREADS = 320;
+constexpr int KP_MAX = 4096;  // K panel per launch (integer accumulators sized for <= 16 chunks)
 
-int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, double alpha,
-             const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
-             int levels) {
-  (void)h; (void)ta; (void)tb; (void)uplo; (void)m; (void)n; (void)k; (void)alpha; (void)A; (void)lda;
-  (void)B; (void)ldb; (void)beta; (void)C; (void)ldc; (void)levels;
-  return GEP_ERR_UNSUPPORTED;
+// ------------------------------------------------------------------ splitting
+
+// e[r] with max_kk |X(r,kk)| < 2^e[r] (0 for an all-zero row); X(r,kk) = X[r*sr + kk*sk].
+__global__ void k_rowexp(int R, int K, const double* __restrict__ X, long long sr, long long sk, int* __restrict__ e,
+                         const int* st) {
+  if (status_bad(st)) return;
+  if (sk == 1) {  // warp per row, contiguous along kk
+    int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (r >= R) return;
+    double m = 0.0;
+    for (int kk = lane; kk < K; kk += 32) m = fmax(m, fabs(X[r * sr + kk]));
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) e[r] = (m > 0.0) ? ilogb(m) + 1 : 0;
+  } else {  // thread per row, consecutive rows contiguous
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    double m = 0.0;
+    for (int kk = 0; kk < K; ++kk) m = fmax(m, fabs(X[r + kk * sk]));
+    e[r] = (m > 0.0) ? ilogb(m) + 1 : 0;
+  }
+}
+
+// Digit planes out[s][r][kk] (bf16, kk contiguous, Kpad columns, zero padding).
+__global__ void __launch_bounds__(256) k_split(int R, int K, int Kpad, const double* __restrict__ X, long long sr,
+                                               long long sk, const int* __restrict__ e, int S,
+                                               __nv_bfloat16* __restrict__ out, const int* st) {
+  __shared__ double t[32][33];
+  if (status_bad(st)) return;
+  int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int q = ty; q < 32; q += 8) {
+    int r, kk;
+    if (sk == 1) { r = r0 + q; kk = k0 + tx; }
+    else { r = r0 + tx; kk = k0 + q; }
+    double v = 0.0;
+    if (r < R && kk < K) v = X[r * sr + kk * sk];
+    if (sk == 1) t[q][tx] = v; else t[tx][q] = v;
+  }
+  __syncthreads();
+  for (int q = ty; q < 32; q += 8) {
+    int r = r0 + q, kk = k0 + tx;
+    if (r >= R || kk >= Kpad) continue;
+    double x = (kk < K) ? ldexp(t[q][tx], -e[r]) : 0.0;
+    size_t base = (size_t)r * Kpad + kk;
+    size_t plane = (size_t)R * Kpad;
+    for (int s = 0; s < S; ++s) {
+      double y = x * 128.0;
+      double d = rint(y);
+      x = y - d;
+      out[base + (size_t)s * plane] = __double2bfloat16(d);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after ~4 s of wall time and records a timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* st) {
+  if (mbar_try(bar, parity)) return true;
+  unsigned long long t0 = gtimer();
+  for (;;) {
+    if (mbar_try(bar, parity)) return true;
+    if (gtimer() - t0 > 4000000000ull) {
+      atomicExch(st + 1, GEP_ERR_TIMEOUT);
+      return false;
+    }
+    if (*(volatile int*)(st + 1) != 0) return false;  // another CTA already gave up
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(dst), "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)map) : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);   // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 46;                   // descriptor version (sm_100 family)
+  d |= (uint64_t)4 << 61;                   // layout: SWIZZLE_64B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D f32, A/B bf16, both K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }"
+      ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// T = hi * 2^D + lo as a 128-bit two's-complement integer (0 <= D < 64), returned
+// as the double nearest to T * 2^adj (round to nearest even), built with integer
+// operations only: the FP64 pipe of this part is ~60x slower than its integer ALUs.
+// Falls back to FP64 arithmetic when the result would be subnormal or overflow.
+__device__ __forceinline__ double fixed_to_double(long long hi, long long lo, int D, int adj) {
+  unsigned long long tl, th;
+  if (D == 0) {
+    tl = (unsigned long long)hi + (unsigned long long)lo;
+    unsigned long long c = tl < (unsigned long long)hi ? 1ull : 0ull;
+    th = (unsigned long long)(hi >> 63) + (unsigned long long)(lo >> 63) + c;
+  } else {
+    unsigned long long a = (unsigned long long)hi << D;
+    unsigned long long ah = (unsigned long long)(hi >> (64 - D));
+    tl = a + (unsigned long long)lo;
+    unsigned long long c = tl < a ? 1ull : 0ull;
+    th = ah + (unsigned long long)(lo >> 63) + c;
+  }
+  unsigned long long sign = th >> 63;
+  if (sign) {  // magnitude of the 128-bit value
+    tl = ~tl + 1ull;
+    th = ~th + (tl == 0ull ? 1ull : 0ull);
+  }
+  if ((th | tl) == 0ull) return 0.0;
+  int p;  // position of the leading one
+  if (th) p = 127 - __clzll((long long)th);
+  else p = 63 - __clzll((long long)tl);
+  unsigned long long m;
+  if (p <= 52) {
+    m = tl << (52 - p);
+  } else {
+    int sh = p - 52;  // 1 .. 75
+    unsigned long long rem_hi, rem_lo, half_hi, half_lo;
+    if (sh < 64) {
+      m = (tl >> sh) | (sh ? (th << (64 - sh)) : 0ull);
+      rem_lo = tl & ((1ull << sh) - 1ull);
+      rem_hi = 0ull;
+      half_lo = 1ull << (sh - 1);
+      half_hi = 0ull;
+    } else {
+      int s2 = sh - 64;
+      m = th >> s2;
+      rem_lo = tl;
+      rem_hi = s2 ? (th & ((1ull << s2) - 1ull)) : 0ull;
+      if (s2 == 0) { half_hi = 0ull; half_lo = 1ull << 63; }
+      else { half_hi = 1ull << (s2 - 1); half_lo = 0ull; }
+    }
+    bool gt = (rem_hi > half_hi) || (rem_hi == half_hi && rem_lo > half_lo);
+    bool eq = (rem_hi == half_hi) && (rem_lo == half_lo);
+    if (gt || (eq && (m & 1ull))) {
+      ++m;
+      if (m >> 53) { m >>= 1; ++p; }
+    }
+  }
+  int ex = p + adj + 1023;
+  if (ex <= 0 || ex >= 2047) {  // outside the normal range: let FP64 arithmetic handle it
+    double v = ldexp((double)(m & ((1ull << 53) - 1ull)), p - 52 + adj);
+    return sign ? -v : v;
+  }
+  unsigned long long bits = (sign << 63) | ((unsigned long long)ex << 52) | (m & ((1ull << 52) - 1ull));
+  return __longlong_as_double((long long)bits);
+}
+
+struct OzArgs {
+  int m, n, kpad, S, lmax, lower;
+  const int* ea;
+  const int* eb;
+  double alpha, beta;
+  double* C;
+  int ldc;
+  int* st;
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__ CUtensorMap tmA,
+                                                          const __grid_constant__ CUtensorMap tmB, OzArgs p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bars[2 * STAGES + 3];
+  __shared__ uint32_t tmem_slot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tm = blockIdx.x * TM, tn = blockIdx.y * TN;
+  __shared__ int skip;
+  if (p.lower && tm + TM - 1 < tn) return;  // tile strictly above the diagonal (uniform)
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int S = p.S, LMAX = p.lmax;
+  const uint32_t a_bytes = (uint32_t)S * TM * TK * 2, b_bytes = (uint32_t)S * TN * TK * 2;
+  const uint32_t stage_bytes = a_bytes + b_bytes;
+  const uint32_t bar_full = smem_u32(&bars[0]), bar_empty = smem_u32(&bars[STAGES]);
+  const uint32_t bar_accf = smem_u32(&bars[2 * STAGES]), bar_acce = smem_u32(&bars[2 * STAGES + 1]);
+  const uint32_t bar_done = smem_u32(&bars[2 * STAGES + 2]);
+  const int nsteps = p.kpad / TK;
+  const int nchunks = (p.kpad + KCH - 1) / KCH;
+  const int nlev = LMAX - 1;  // levels 2..LMAX
+
+  if (threadIdx.x == 0) {
+    skip = status_bad(p.st) ? 1 : 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(bar_full + 8 * s, 1);
+      mbar_init(bar_empty + 8 * s, 1);
+    }
+    mbar_init(bar_accf, 1);
+    mbar_init(bar_acce, 8);
+    mbar_init(bar_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    prefetch_map(&tmA);
+    prefetch_map(&tmB);
+  }
+  __syncthreads();
+  if (skip) return;  // one decision for the whole CTA
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      bool ok = true;
+      for (int step = 0; step < nsteps && ok; ++step) {
+        int sidx = step % STAGES;
+        uint32_t ph = (uint32_t)(step / STAGES) & 1u;
+        ok = mbar_wait(bar_empty + 8 * sidx, ph ^ 1u, p.st);
+        if (!ok) break;
+        uint32_t dst = smem_u32(smem + (size_t)sidx * stage_bytes);
+        mbar_expect_tx(bar_full + 8 * sidx, stage_bytes);
+        tma_load_3d(dst, &tmA, step * TK, tm, 0, bar_full + 8 * sidx);
+        tma_load_3d(dst + a_bytes, &tmB, step * TK, tn, 0, bar_full + 8 * sidx);
+        issued = step + 1;
+      }
+      // make sure every copy this thread started has landed before the CTA retires
+      for (int step = (issued > STAGES ? issued - STAGES : 0); step < issued; ++step)
+        mbar_wait(bar_full + 8 * (step % STAGES), (uint32_t)(step / STAGES) & 1u, p.st);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = true;
+      int step = 0;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        ok = mbar_wait(bar_acce, ((uint32_t)c & 1u) ^ 1u, p.st);
+        if (!ok) break;
+        tc_fence_after();
+        int send = min(nsteps, (c + 1) * (KCH / TK));
+        for (int sic = 0; step < send; ++step, ++sic) {
+          int sidx = step % STAGES;
+          ok = mbar_wait(bar_full + 8 * sidx, (uint32_t)(step / STAGES) & 1u, p.st);
+          if (!ok) break;
+          tc_fence_after();
+          uint32_t abase = smem_u32(smem + (size_t)sidx * stage_bytes);
+          uint32_t bbase = abase + a_bytes;
+#pragma unroll 1
+          for (int kk = 0; kk < TK / 16; ++kk) {
+            for (int s = 1; s <= S; ++s) {
+              int tmax = min(S, LMAX - s);
+              if (tmax < 1) break;
+              uint64_t adesc = sdesc_sw64(abase + (uint32_t)(s - 1) * TM * TK * 2 + kk * 32);
+              for (int t0 = 1; t0 <= tmax; t0 += 4) {
+                int nt = min(4, tmax - t0 + 1);
+                uint64_t bdesc = sdesc_sw64(bbase + (uint32_t)(t0 - 1) * TN * TK * 2 + kk * 32);
+                uint32_t col = (uint32_t)(s + t0 - 2) * TN;
+                uint32_t acc = (sic == 0 && kk == 0 && s == 1) ? 0u : 1u;
+                umma(tmem + col, adesc, bdesc, idesc_bf16(nt * TN), acc);
+              }
+            }
+          }
+          umma_commit(bar_empty + 8 * sidx);  // frees the stage once these MMAs are done
+        }
+        if (!ok) break;
+        umma_commit(bar_accf);
+      }
+      umma_commit(bar_done);
+      mbar_wait(bar_done, 0, p.st);
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32*(w%4).., columns 32*((w-2)/4)..
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    const int row = tm + q * 32 + lane;
+    long long hi[32], lo[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) { hi[j] = 0; lo[j] = 0; }
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      ok = mbar_wait(bar_accf, (uint32_t)c & 1u, p.st);
+      if (!ok) break;
+      tc_fence_after();
+      for (int lv = 0; lv < nlev; ++lv) {
+        int l = lv + 2;
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(lv * TN + half * 32), v);
+        if (l <= 4) {
+          int sh = 7 * (4 - l);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) hi[j] += (long long)__float2int_rn(v[j]) * (1ll << sh);
+        } else {
+          int sh = 7 * (LMAX - l);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) lo[j] += (long long)__float2int_rn(v[j]) * (1ll << sh);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_acce);
+    }
+    if (ok && row < p.m) {
+      const int ea = p.ea[row];
+      const bool two = LMAX >= 5;  // a second (low) accumulator is in use
+      const int D = two ? 7 * LMAX - 28 : 0;
+      const int base_adj = ea - (two ? 7 * LMAX : 28);
+      const double alpha = p.alpha, beta = p.beta;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        int col = tn + half * 32 + j;
+        if (col >= p.n || (p.lower && row < col)) continue;
+        double v = fixed_to_double(hi[j], two ? lo[j] : 0ll, D, base_adj + p.eb[col]);
+        double* cp = p.C + (size_t)row + (size_t)col * p.ldc;
+        double out = (alpha == 1.0) ? v : (alpha == -1.0 ? -v : alpha * v);
+        if (beta != 0.0) out = fma(beta, *cp, out);
+        *cp = out;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+size_t smem_bytes_for(int S) { return (size_t)STAGES * S * (TM + TN) * TK * 2 + 1024; }
+
+// cuTensorMapEncodeTiled is a driver-API call; it is resolved at run time through the
+// runtime's entry-point query so the library does not link libcuda directly (it then
+// loads on machines without a GPU driver, e.g. for symbol checks).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+int encode_map(CUtensorMap* map, const void* base, int kpad, int rows, int S, int box_rows) {
+  cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)S};
+  cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)kpad * 2 * (cuuint64_t)rows};
+  cuuint32_t box[3] = {(cuuint32_t)TK, (cuuint32_t)box_rows, (cuuint32_t)S};
+  cuuint32_t estr[3] = {1, 1, 1};
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) {
+    fprintf(stderr, "gep: cuTensorMapEncodeTiled not available from the driver\n");
+    return GEP_ERR_CUDA;
+  }
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    fprintf(stderr, "gep: cuTensorMapEncodeTiled failed (%d)\n", (int)r);
+    return GEP_ERR_CUDA;
+  }
+  return GEP_OK;
+}
+
+}  // namespace
+
+size_t oz_workspace_bytes(int m, int n, int k) {
+  int kp = k < KP_MAX ? k : KP_MAX;
+  size_t kpad = (size_t)((kp + TK - 1) / TK) * TK;
+  return align256((size_t)MAXS * (m + n) * kpad * 2) + align256((size_t)(m + n) * 4) + 1024;
+}
+
+int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, double alpha, const double* A,
+             int lda, const double* B, int ldb, double beta, double* C, int ldc, int levels) {
+  if (m <= 0 || n <= 0) return GEP_OK;
+  if (k <= 0 || alpha == 0.0) return dgemm_f64(h, ta, tb, uplo, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+  const int S = levels - 1;
+  if (S < 1 || S > MAXS) return GEP_ERR_UNSUPPORTED;
+  bool TA = (ta == 'T' || ta == 't'), TB = (tb == 'T' || tb == 't');
+  // view of op(A) as rows i, depth kk: element at A[i*sra + kk*ska]
+  long long sra = TA ? lda : 1, ska = TA ? 1 : lda;
+  // view of op(B)^T as rows j, depth kk
+  long long srb = TB ? 1 : ldb, skb = TB ? ldb : 1;
+  // scratch
+  size_t cap = h->eng_bytes;
+  char* base = h->eng_ws;
+  size_t per_k = (size_t)S * (m + n) * 2;
+  size_t fixed = align256((size_t)(m + n) * 4) + 1024;
+  if (base == nullptr || cap <= fixed) return GEP_ERR_ALLOC;
+  long long kp_fit = (long long)((cap - fixed) / per_k) / TK * TK;
+  int KP = (int)(kp_fit < KP_MAX ? kp_fit : KP_MAX);
+  if (KP < TK) return GEP_ERR_ALLOC;
+  static int attr_done = 0;
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes_for(MAXS));
+    attr_done = 1;
+  }
+  int lower = (uplo == 'L' || uplo == 'l');
+  for (int kb = 0; kb < k; kb += KP) {
+    int kc = min(KP, k - kb);
+    int kpad = (kc + TK - 1) / TK * TK;
+    char* p = base;
+    __nv_bfloat16* As = (__nv_bfloat16*)p;
+    p += align256((size_t)S * m * kpad * 2);
+    __nv_bfloat16* Bs = (__nv_bfloat16*)p;
+    p += align256((size_t)S * n * kpad * 2);
+    int* ea = (int*)p;
+    int* eb = ea + m;
+    const double* Ap = A + (size_t)kb * ska;
+    const double* Bp = B + (size_t)kb * skb;
+    if (ska == 1) k_rowexp<<<(m * 32 + 255) / 256, 256, 0, h->stream>>>(m, kc, Ap, sra, ska, ea, h->d_status);
+    else k_rowexp<<<(m + 255) / 256, 256, 0, h->stream>>>(m, kc, Ap, sra, ska, ea, h->d_status);
+    GEP_CHECK(check_launch(h));
+    if (skb == 1) k_rowexp<<<(n * 32 + 255) / 256, 256, 0, h->stream>>>(n, kc, Bp, srb, skb, eb, h->d_status);
+    else k_rowexp<<<(n + 255) / 256, 256, 0, h->stream>>>(n, kc, Bp, srb, skb, eb, h->d_status);
+    GEP_CHECK(check_launch(h));
+    k_split<<<dim3(kpad / 32, (m + 31) / 32), 256, 0, h->stream>>>(m, kc, kpad, Ap, sra, ska, ea, S, As, h->d_status);
+    GEP_CHECK(check_launch(h));
+    k_split<<<dim3(kpad / 32, (n + 31) / 32), 256, 0, h->stream>>>(n, kc, kpad, Bp, srb, skb, eb, S, Bs, h->d_status);
+    GEP_CHECK(check_launch(h));
+    CUtensorMap mA, mB;
+    GEP_CHECK(encode_map(&mA, As, kpad, m, S, TM));
+    GEP_CHECK(encode_map(&mB, Bs, kpad, n, S, TN));
+    OzArgs a;
+    a.m = m; a.n = n; a.kpad = kpad; a.S = S; a.lmax = levels; a.lower = lower;
+    a.ea = ea; a.eb = eb; a.alpha = alpha; a.beta = (kb == 0) ? beta : 1.0; a.C = C; a.ldc = ldc; a.st = h->d_status;
+    dim3 grid((m + TM - 1) / TM, (n + TN - 1) / TN);
+    int slot = -1;
+    if (h->prof_on) {
+      if (h->prof_used < h->prof_cap) {
+        slot = h->prof_used++;
+        cudaEventRecord(h->prof_ev[2 * slot], h->stream);
+        int npairs = 0;
+        for (int s = 1; s <= S; ++s) npairs += max(0, min(S, levels - s));
+        double f = 2.0 * m * n * (double)kc * (lower ? 0.5 : 1.0);
+        h->prof_f64eq[slot] = f;
+        h->prof_flops[slot] = f * npairs;
+      } else {
+        h->prof_skipped++;
+      }
+    }
+    k_oz_gemm<<<grid, NTHREADS, smem_bytes_for(S), h->stream>>>(mA, mB, a);
+    GEP_CHECK(check_launch(h));
+    if (slot >= 0) cudaEventRecord(h->prof_ev[2 * slot + 1], h->stream);
+  }
+  return GEP_OK;
 }
 
 }  // namespace gep

@@ -13,11 +13,20 @@ struct gep_handle_s {
   int* d_status = nullptr;   // [0] numerical info, [1] error code (timeouts etc.)
   char* ws = nullptr;        // caller workspace
   size_t ws_bytes = 0;
+  char* eng_ws = nullptr;    // scratch of the split-BF16 product engine
+  size_t eng_bytes = 0;
   long long launches = 0;
   int sm_count = 152;
   int magic = 0x6e70;
   cudaEvent_t ev[8] = {};
   bool timers_recorded = false;
+  // optional per-launch timing of the tensor-core product kernel
+  int prof_on = 0;
+  int prof_cap = 0, prof_used = 0;
+  long long prof_skipped = 0;
+  cudaEvent_t* prof_ev = nullptr;   // 2 * prof_cap events
+  double* prof_flops = nullptr;     // tensor flops of each recorded launch
+  double* prof_f64eq = nullptr;     // FP64-equivalent flops of each recorded launch
 };
 
 namespace gep {

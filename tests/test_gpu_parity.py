@@ -201,15 +201,16 @@ def _check_solution(A, B, w, Y, w_ref):
     assert orth <= 1e-12, orth
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp64_emulated"])
 @pytest.mark.parametrize("reducer", ["twosided", "explicit_inv"])
 @pytest.mark.parametrize("seed", [0, 1])
-def test_solve_known_spectrum_M512(gep, oracle_lib, reducer, seed):
+def test_solve_known_spectrum_M512(gep, oracle_lib, reducer, seed, precision):
     """Workload of the M=512 known-spectrum configuration: exact lambda and the oracle."""
     g = gi.known_spectrum(512, seed)
     A, B = g["A"], g["B"]
     w_ref, Y_ref, info = oracle_lib.gep_solve(A, B)
     assert info == 0
-    w, Y, info = gep.solve(dev(A), dev(B), reducer=reducer)
+    w, Y, info = gep.solve(dev(A), dev(B), reducer=reducer, precision=precision)
     assert info == 0
     wh, Yh = host(w), host(Y)
     _check_solution(A, B, wh, Yh, w_ref)
@@ -220,16 +221,17 @@ def test_solve_known_spectrum_M512(gep, oracle_lib, reducer, seed):
     assert np.max(np.abs(Yh[:, iso] - Y_ref[:, iso])) <= 1e-8
 
 
-@pytest.mark.parametrize("M", [4, 36, 260, 516])
-def test_solve_tight_binding_vs_oracle(gep, oracle_lib, M):
+@pytest.mark.parametrize("precision", ["fp64", "fp64_emulated"])
+@pytest.mark.parametrize("M", [4, 36, 260, 516, 1280])
+def test_solve_tight_binding_vs_oracle(gep, oracle_lib, M, precision):
     tb = gi.tight_binding(M, seed=M)
     A, B = tb["A"], tb["B"]
     w_ref, Y_ref, info = oracle_lib.gep_solve(A, B)
     assert info == 0
-    w, Y, info = gep.solve(dev(A), dev(B))
+    w, Y, info = gep.solve(dev(A), dev(B), precision=precision)
     assert info == 0
     _check_solution(A, B, host(w), host(Y), w_ref)
-    w0, Y0, info0 = gep.solve(dev(A), dev(B), want_vectors=False)
+    w0, Y0, info0 = gep.solve(dev(A), dev(B), want_vectors=False, precision=precision)
     assert Y0 is None and info0 == 0
     assert np.max(np.abs(host(w0) - w_ref)) <= 1e-11 * two_norm(A)
 
