@@ -42,7 +42,41 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-check", action="store_true")
+    p.add_argument("--gemm", type=int, nargs=3, metavar=("m", "n", "k"),
+                   help="time only the split-BF16 product engine on an m x n x k product (profiling aid)")
     return p.parse_args()
+
+
+def run_gemm(a):
+    """Engine-only timing (used for ncu captures of the product kernel on a small case)."""
+    import torch
+    from paper_1504_06443_gb300 import build as gbuild
+    import paper_1504_06443_gb300 as gep
+    gbuild.build()
+    m, n, k = a.gemm
+    g = torch.Generator(device="cuda").manual_seed(a.seed)
+    A = torch.randn(m, k, dtype=torch.float64, device="cuda", generator=g)
+    B = torch.randn(k, n, dtype=torch.float64, device="cuda", generator=g)
+    C = torch.zeros((n, m), dtype=torch.float64, device="cuda").t()
+    h = gep.default_handle()
+    for _ in range(a.warmup):
+        gep.dgemm(A, B, engine=a.precision, C=C, handle=h)
+    torch.cuda.synchronize()
+    h.profile_enable(4096)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        gep.dgemm(A, B, engine=a.precision, C=C, handle=h)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = h.profile_read()
+    h.profile_enable(0)
+    ms = e0.elapsed_time(e1) / a.steps
+    print(json.dumps({"gemm": [m, n, k], "engine": a.precision, "ms_per_call": ms,
+                      "fp64_equiv_tflops": 2.0 * m * n * k / (ms * 1e-3) / 1e12,
+                      "kernel_ms_per_call": prof["ms"] / max(1, a.steps),
+                      "kernel_tensor_tflops": prof["tensor_flops"] / (prof["ms"] * 1e-3) / 1e12 if prof["ms"] else None}),
+          flush=True)
 
 
 def peaks():
@@ -171,6 +205,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.gemm:
+        run_gemm(a)
+        return
     if a.impl == "reference":
         if world > 1:
             import torch.distributed as dist

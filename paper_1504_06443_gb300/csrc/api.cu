@@ -100,6 +100,12 @@ int gep_create(gep_handle_t* out, void* stream) {
   cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev);
   if (cudaMalloc((void**)&h->d_status, 256) != cudaSuccess) { delete h; return GEP_ERR_CUDA; }
   if (cudaMemset(h->d_status, 0, 256) != cudaSuccess) { cudaFree(h->d_status); delete h; return GEP_ERR_CUDA; }
+  h->splitk_bytes = (size_t)32 << 20;
+  if (cudaMalloc((void**)&h->d_splitk, h->splitk_bytes) != cudaSuccess) {
+    cudaFree(h->d_status);
+    delete h;
+    return GEP_ERR_CUDA;
+  }
   for (int i = 0; i < 8; ++i) cudaEventCreate(&h->ev[i]);
   *out = h;
   return GEP_OK;
@@ -110,6 +116,7 @@ int gep_destroy(gep_handle_t h) {
   gep_profile_enable(h, 0);
   for (int i = 0; i < 8; ++i) cudaEventDestroy(h->ev[i]);
   cudaFree(h->d_status);
+  cudaFree(h->d_splitk);
   h->magic = 0;
   delete h;
   return GEP_OK;

@@ -88,6 +88,88 @@ __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int k, double alpha
   }
 }
 
+// Split-K partial products for small outputs with long K: CTA (bi, bj, z) computes the
+// 64 x 64 tile over k in [z*kc, (z+1)*kc) into P[z] (m x n, leading dimension m).
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_dgemm_splitk(int m, int n, int k, int kc, const double* __restrict__ A,
+                                                      int lda, const double* __restrict__ B, int ldb,
+                                                      double* __restrict__ P, const int* __restrict__ st) {
+  if (status_bad(st)) return;
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int bi = blockIdx.x, bj = blockIdx.y, z = blockIdx.z;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int row0 = bi * BM, col0 = bj * BN;
+  const int kb = z * kc, ke = min(k, kb + kc);
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+  for (int k0 = kb; k0 < ke; k0 += BK) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int idx = tid + r * 256;
+      int i, kk;
+      if (!TA) { i = idx & 63; kk = idx >> 6; }
+      else { kk = idx & 15; i = idx >> 4; }
+      int gi = row0 + i, gk = k0 + kk;
+      double v = 0.0;
+      if (gi < m && gk < ke) v = TA ? A[GEP_IX(gk, gi, lda)] : A[GEP_IX(gi, gk, lda)];
+      As[kk][i] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int idx = tid + r * 256;
+      int j, kk;
+      if (!TB) { kk = idx & 15; j = idx >> 4; }
+      else { j = idx & 63; kk = idx >> 6; }
+      int gj = col0 + j, gk = k0 + kk;
+      double v = 0.0;
+      if (gj < n && gk < ke) v = TB ? B[GEP_IX(gj, gk, ldb)] : B[GEP_IX(gk, gj, ldb)];
+      Bs[kk][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][tx + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][ty + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+  double* Pz = P + (size_t)z * m * n;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    int j = col0 + ty + 16 * c;
+    if (j >= n) continue;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int i = row0 + tx + 16 * r;
+      if (i < m) Pz[(size_t)i + (size_t)j * m] = acc[r][c];
+    }
+  }
+}
+
+// C = alpha * sum_z P[z] + beta * C, summed in a fixed order (deterministic).
+__global__ void k_splitk_reduce(int m, int n, int nz, const double* __restrict__ P, double alpha, double beta,
+                                double* __restrict__ C, int ldc, int lower, const int* __restrict__ st) {
+  if (status_bad(st)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= m || j >= n || (lower && i < j)) return;
+  double s = 0.0;
+  for (int z = 0; z < nz; ++z) s += P[(size_t)z * m * n + (size_t)i + (size_t)j * m];
+  double v = alpha * s;
+  if (beta != 0.0) v = fma(beta, C[GEP_IX(i, j, ldc)], v);
+  C[GEP_IX(i, j, ldc)] = v;
+}
+
 __global__ void k_scale(int m, int n, double beta, double* C, int ldc, int lower,
                         const int* __restrict__ st) {
   if (status_bad(st)) return;
@@ -111,6 +193,29 @@ int dgemm_f64(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, 
   }
   bool TA = (ta == 'T' || ta == 't'), TB = (tb == 'T' || tb == 't');
   dim3 grid((m + BM - 1) / BM, (n + BN - 1) / BN);
+  long long tiles = (long long)grid.x * grid.y;
+  // A few output tiles with a long K leave most SMs idle: split K across CTAs.
+  if (tiles < h->sm_count && k >= 1024 && h->d_splitk != nullptr) {
+    long long nz = (2LL * h->sm_count + tiles - 1) / tiles;
+    nz = nz < k / 256 ? nz : k / 256;
+    long long cap = (long long)(h->splitk_bytes / (sizeof(double) * (size_t)m * n));
+    nz = nz < cap ? nz : cap;
+    if (nz >= 2) {
+      int kc = (int)((k + nz - 1) / nz);
+      kc = (kc + BK - 1) / BK * BK;
+      int z = (k + kc - 1) / kc;
+      dim3 g3(grid.x, grid.y, z);
+      double* P = h->d_splitk;
+      if (!TA && !TB) k_dgemm_splitk<false, false><<<g3, 256, 0, h->stream>>>(m, n, k, kc, A, lda, B, ldb, P, h->d_status);
+      else if (!TA && TB) k_dgemm_splitk<false, true><<<g3, 256, 0, h->stream>>>(m, n, k, kc, A, lda, B, ldb, P, h->d_status);
+      else if (TA && !TB) k_dgemm_splitk<true, false><<<g3, 256, 0, h->stream>>>(m, n, k, kc, A, lda, B, ldb, P, h->d_status);
+      else k_dgemm_splitk<true, true><<<g3, 256, 0, h->stream>>>(m, n, k, kc, A, lda, B, ldb, P, h->d_status);
+      GEP_CHECK(check_launch(h));
+      dim3 gr((m + 255) / 256, n);
+      k_splitk_reduce<<<gr, 256, 0, h->stream>>>(m, n, z, P, alpha, beta, C, ldc, lower, h->d_status);
+      return check_launch(h);
+    }
+  }
   if (!TA && !TB)
     k_dgemm<false, false><<<grid, 256, 0, h->stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, lower, h->d_status);
   else if (!TA && TB)

@@ -40,30 +40,50 @@ constexpr int KP_MAX = 4096;  // K panel per launch (integer accumulators sized 
 
 // ------------------------------------------------------------------ splitting
 
+// Both splitting kernels work on the IEEE bit patterns with integer instructions
+// only: the FP64 pipe of this part is far slower than its integer ALUs, and with
+// FP64 arithmetic the split would cost more than the tensor-core product it feeds.
+
+// Biased exponent field of |x| (0 for zero / subnormal).
+__device__ __forceinline__ int exp_field(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+
 // e[r] with max_kk |X(r,kk)| < 2^e[r] (0 for an all-zero row); X(r,kk) = X[r*sr + kk*sk].
+// For a normal x with biased exponent E, |x| < 2^(E-1022).
 __global__ void k_rowexp(int R, int K, const double* __restrict__ X, long long sr, long long sk, int* __restrict__ e,
                          const int* st) {
   if (status_bad(st)) return;
   if (sk == 1) {  // warp per row, contiguous along kk
     int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (r >= R) return;
-    double m = 0.0;
-    for (int kk = lane; kk < K; kk += 32) m = fmax(m, fabs(X[r * sr + kk]));
-    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) e[r] = (m > 0.0) ? ilogb(m) + 1 : 0;
+    int m = 0;
+    for (int kk = lane; kk < K; kk += 32) m = max(m, exp_field(X[r * sr + kk]));
+    for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) e[r] = m ? m - 1022 : 0;
   } else {  // thread per row, consecutive rows contiguous
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
-    double m = 0.0;
-    for (int kk = 0; kk < K; ++kk) m = fmax(m, fabs(X[r + kk * sk]));
-    e[r] = (m > 0.0) ? ilogb(m) + 1 : 0;
+    int m = 0;
+    for (int kk = 0; kk < K; ++kk) m = max(m, exp_field(X[r + kk * sk]));
+    e[r] = m ? m - 1022 : 0;
   }
 }
 
+// Exact BF16 bit pattern of a small integer d (|d| <= 256).
+__device__ __forceinline__ unsigned short bf16_of_int(int d) {
+  if (d == 0) return 0;
+  unsigned a = (unsigned)(d < 0 ? -d : d);
+  int p = 31 - __clz((int)a);
+  unsigned mant = (a << (7 - p)) & 0x7Fu;
+  return (unsigned short)(((d < 0) ? 0x8000u : 0u) | ((unsigned)(127 + p) << 7) | mant);
+}
+
 // Digit planes out[s][r][kk] (bf16, kk contiguous, Kpad columns, zero padding).
+// x 2^-e[r] is rounded to the integer F = round(x 2^(7S-e)) (|F| < 2^(7S)), whose
+// balanced base-128 digits are peeled off from the least significant end:
+// d_S..d_2 in [-64, 63], the leading d_1 in [-128, 128].  Plane s-1 holds d_s.
 __global__ void __launch_bounds__(256) k_split(int R, int K, int Kpad, const double* __restrict__ X, long long sr,
                                                long long sk, const int* __restrict__ e, int S,
-                                               __nv_bfloat16* __restrict__ out, const int* st) {
+                                               unsigned short* __restrict__ out, const int* st) {
   __shared__ double t[32][33];
   if (status_bad(st)) return;
   int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
@@ -80,15 +100,36 @@ __global__ void __launch_bounds__(256) k_split(int R, int K, int Kpad, const dou
   for (int q = ty; q < 32; q += 8) {
     int r = r0 + q, kk = k0 + tx;
     if (r >= R || kk >= Kpad) continue;
-    double x = (kk < K) ? ldexp(t[q][tx], -e[r]) : 0.0;
+    long long F = 0;
+    if (kk < K) {
+      long long bits = __double_as_longlong(t[q][tx]);
+      int E = (int)((bits >> 52) & 0x7FF);
+      if (E != 0) {
+        unsigned long long m = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        int sh = E - 1075 + 7 * S - e[r];
+        unsigned long long qv;
+        if (sh >= 0) {
+          qv = m << sh;
+        } else if (sh > -64) {
+          int rs = -sh;
+          qv = m >> rs;
+          unsigned long long rem = m & ((1ull << rs) - 1ull), half = 1ull << (rs - 1);
+          if (rem > half || (rem == half && (qv & 1ull))) ++qv;
+        } else {
+          qv = 0;
+        }
+        F = (bits < 0) ? -(long long)qv : (long long)qv;
+      }
+    }
     size_t base = (size_t)r * Kpad + kk;
     size_t plane = (size_t)R * Kpad;
-    for (int s = 0; s < S; ++s) {
-      double y = x * 128.0;
-      double d = rint(y);
-      x = y - d;
-      out[base + (size_t)s * plane] = __double2bfloat16(d);
+    for (int s = S - 1; s >= 1; --s) {
+      int d = (int)(F & 127);
+      if (d >= 64) d -= 128;
+      F = (F - d) >> 7;
+      out[base + (size_t)s * plane] = bf16_of_int(d);
     }
+    out[base] = bf16_of_int((int)F);
   }
 }
 
@@ -506,9 +547,9 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
     int kc = min(KP, k - kb);
     int kpad = (kc + TK - 1) / TK * TK;
     char* p = base;
-    __nv_bfloat16* As = (__nv_bfloat16*)p;
+    unsigned short* As = (unsigned short*)p;  // bf16 bit patterns
     p += align256((size_t)S * m * kpad * 2);
-    __nv_bfloat16* Bs = (__nv_bfloat16*)p;
+    unsigned short* Bs = (unsigned short*)p;
     p += align256((size_t)S * n * kpad * 2);
     int* ea = (int*)p;
     int* eb = ea + m;

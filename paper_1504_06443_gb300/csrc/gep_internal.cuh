@@ -15,6 +15,8 @@ struct gep_handle_s {
   size_t ws_bytes = 0;
   char* eng_ws = nullptr;    // scratch of the split-BF16 product engine
   size_t eng_bytes = 0;
+  double* d_splitk = nullptr;  // handle-owned partial sums of split-K FP64 products
+  size_t splitk_bytes = 0;
   long long launches = 0;
   int sm_count = 152;
   int magic = 0x6e70;

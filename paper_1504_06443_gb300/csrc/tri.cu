@@ -132,63 +132,103 @@ int tri_inv_diag_blocks(gep_handle_t h, int M, const double* L, int ldl, double*
   return check_launch(h);
 }
 
-// X := L^-1 X, blocked forward substitution; tmp holds NB x n.
+// All triangular solves and the Cholesky factorisation below recurse on halves whose
+// split points are multiples of NB, down to the NB x NB diagonal blocks (leaf o covers
+// rows o .. o+NB-1 and uses invD block o/NB).  The off-diagonal work is then a few
+// products with a long inner dimension (n/2, n/4, ...), which the tensor-core engine
+// runs near its best rate, instead of many rank-NB updates.
+namespace {
+
+int split_nb(int n) { return ((n / NB + 1) / 2) * NB; }
+
+// rows [o, o+n) of X (X points at row o) := L(o:o+n, o:o+n)^-1 X
+int lln_rec(gep_handle_t h, int o, int n, int ncol, const double* L, int ldl, const double* invD, double* X, int ldx,
+            double* tmp, int engine) {
+  if (n <= NB) {
+    const double* Dk = invD + (size_t)(o / NB) * NB * NB;
+    GEP_CHECK(dgemm(h, 'N', 'N', 'F', n, ncol, n, 1.0, Dk, NB, X, ldx, 0.0, tmp, n, engine));
+    return copy_matrix(h, n, ncol, tmp, n, X, ldx);
+  }
+  int n1 = split_nb(n), n2 = n - n1;
+  GEP_CHECK(lln_rec(h, o, n1, ncol, L, ldl, invD, X, ldx, tmp, engine));
+  GEP_CHECK(dgemm(h, 'N', 'N', 'F', n2, ncol, n1, -1.0, L + GEP_IX(o + n1, o, ldl), ldl, X, ldx, 1.0, X + n1, ldx,
+                  engine));
+  return lln_rec(h, o + n1, n2, ncol, L, ldl, invD, X + n1, ldx, tmp, engine);
+}
+
+// rows [o, o+n) of X := L(o:o+n, o:o+n)^-T X
+int llt_rec(gep_handle_t h, int o, int n, int ncol, const double* L, int ldl, const double* invD, double* X, int ldx,
+            double* tmp, int engine) {
+  if (n <= NB) {
+    const double* Dk = invD + (size_t)(o / NB) * NB * NB;
+    GEP_CHECK(dgemm(h, 'T', 'N', 'F', n, ncol, n, 1.0, Dk, NB, X, ldx, 0.0, tmp, n, engine));
+    return copy_matrix(h, n, ncol, tmp, n, X, ldx);
+  }
+  int n1 = split_nb(n), n2 = n - n1;
+  GEP_CHECK(llt_rec(h, o + n1, n2, ncol, L, ldl, invD, X + n1, ldx, tmp, engine));
+  GEP_CHECK(dgemm(h, 'T', 'N', 'F', n1, ncol, n2, -1.0, L + GEP_IX(o + n1, o, ldl), ldl, X + n1, ldx, 1.0, X, ldx,
+                  engine));
+  return llt_rec(h, o, n1, ncol, L, ldl, invD, X, ldx, tmp, engine);
+}
+
+// X (m x n, columns o .. o+n of the factor) := X L(o:o+n, o:o+n)^-T
+int rlt_rec(gep_handle_t h, int o, int n, int m, const double* L, int ldl, const double* invD, double* X, int ldx,
+            double* tmp, int engine) {
+  if (n <= NB) {
+    const double* Dk = invD + (size_t)(o / NB) * NB * NB;
+    GEP_CHECK(dgemm(h, 'N', 'T', 'F', m, n, n, 1.0, X, ldx, Dk, NB, 0.0, tmp, m, engine));
+    return copy_matrix(h, m, n, tmp, m, X, ldx);
+  }
+  int n1 = split_nb(n), n2 = n - n1;
+  GEP_CHECK(rlt_rec(h, o, n1, m, L, ldl, invD, X, ldx, tmp, engine));
+  GEP_CHECK(dgemm(h, 'N', 'T', 'F', m, n2, n1, -1.0, X, ldx, L + GEP_IX(o + n1, o, ldl), ldl, 1.0,
+                  X + (size_t)n1 * ldx, ldx, engine));
+  return rlt_rec(h, o + n1, n2, m, L, ldl, invD, X + (size_t)n1 * ldx, ldx, tmp, engine);
+}
+
+// Eq. 4 on the diagonal block (o, o) of order n; B points at the full matrix.
+int potrf_rec(gep_handle_t h, int o, int n, double* B, int ldb, double* invD, double* tmp, int engine) {
+  if (n <= NB) {
+    k_potrf_diag<<<1, 256, kSmemDiag, h->stream>>>(n, B + GEP_IX(o, o, ldb), ldb, invD + (size_t)(o / NB) * NB * NB, o,
+                                                   h->d_status);
+    return check_launch(h);
+  }
+  int n1 = split_nb(n), n2 = n - n1;
+  GEP_CHECK(potrf_rec(h, o, n1, B, ldb, invD, tmp, engine));
+  double* L21 = B + GEP_IX(o + n1, o, ldb);
+  GEP_CHECK(rlt_rec(h, o, n1, n2, B, ldb, invD, L21, ldb, tmp, engine));   // L21 = A21 L11^-T
+  GEP_CHECK(dgemm(h, 'N', 'T', 'L', n2, n2, n1, -1.0, L21, ldb, L21, ldb, 1.0, B + GEP_IX(o + n1, o + n1, ldb), ldb,
+                  engine));                                                 // A22 -= L21 L21^T
+  return potrf_rec(h, o + n1, n2, B, ldb, invD, tmp, engine);
+}
+
+}  // namespace
+
+// X := L^-1 X (forward substitution); tmp holds max(NB x n) doubles.
 int trsm_lln(gep_handle_t h, int M, int n, const double* L, int ldl, const double* invD, int nb,
              double* X, int ldx, double* tmp, int engine) {
   if (nb != NB) return GEP_ERR_UNSUPPORTED;
-  for (int kb = 0; kb < M; kb += NB) {
-    int r = min(NB, M - kb);
-    const double* Dk = invD + (size_t)(kb / NB) * NB * NB;
-    GEP_CHECK(dgemm(h, 'N', 'N', 'F', r, n, r, 1.0, Dk, NB, X + kb, ldx, 0.0, tmp, r, engine));
-    GEP_CHECK(copy_matrix(h, r, n, tmp, r, X + kb, ldx));
-    int m2 = M - kb - r;
-    if (m2 > 0)
-      GEP_CHECK(dgemm(h, 'N', 'N', 'F', m2, n, r, -1.0, L + GEP_IX(kb + r, kb, ldl), ldl, X + kb, ldx,
-                      1.0, X + kb + r, ldx, engine));
-  }
-  return GEP_OK;
+  if (M <= 0 || n <= 0) return GEP_OK;
+  return lln_rec(h, 0, M, n, L, ldl, invD, X, ldx, tmp, engine);
 }
 
-// X := L^-T X, blocked backward substitution with the upper triangular L^T.
+// X := L^-T X (backward substitution with the upper triangular L^T).
 int trsm_llt(gep_handle_t h, int M, int n, const double* L, int ldl, const double* invD, int nb,
              double* X, int ldx, double* tmp, int engine) {
   if (nb != NB) return GEP_ERR_UNSUPPORTED;
-  int last = ((M - 1) / NB) * NB;
-  for (int kb = last; kb >= 0; kb -= NB) {
-    int r = min(NB, M - kb);
-    const double* Dk = invD + (size_t)(kb / NB) * NB * NB;
-    GEP_CHECK(dgemm(h, 'T', 'N', 'F', r, n, r, 1.0, Dk, NB, X + kb, ldx, 0.0, tmp, r, engine));
-    GEP_CHECK(copy_matrix(h, r, n, tmp, r, X + kb, ldx));
-    if (kb > 0)
-      GEP_CHECK(dgemm(h, 'T', 'N', 'F', kb, n, r, -1.0, L + kb, ldl, X + kb, ldx, 1.0, X, ldx, engine));
-  }
-  return GEP_OK;
+  if (M <= 0 || n <= 0) return GEP_OK;
+  return llt_rec(h, 0, M, n, L, ldl, invD, X, ldx, tmp, engine);
 }
 
-// Eq. 4: blocked right-looking Cholesky.  invD receives the inverses of the
-// diagonal blocks (reused by the reduction and the back-substitution).  tmp must
-// hold M x NB doubles and follows invD in the caller's workspace.
+// Eq. 4: recursive Cholesky.  invD receives the inverses of the NB x NB diagonal
+// blocks (reused by the reduction and the back-substitution).  tmp (M x NB doubles)
+// follows invD in the caller's workspace.
 int cholesky(gep_handle_t h, int M, double* B, int ldb, double* invD, int engine) {
   if (M <= 0) return GEP_OK;
   set_smem_attr();
   int nblk = (M + NB - 1) / NB;
   double* tmp = invD + (size_t)nblk * NB * NB;
-  for (int kb = 0; kb < M; kb += NB) {
-    int r = min(NB, M - kb);
-    double* Dk = invD + (size_t)(kb / NB) * NB * NB;
-    k_potrf_diag<<<1, 256, kSmemDiag, h->stream>>>(r, B + GEP_IX(kb, kb, ldb), ldb, Dk, kb, h->d_status);
-    GEP_CHECK(check_launch(h));
-    int n2 = M - kb - r;
-    if (n2 <= 0) break;
-    double* P = B + GEP_IX(kb + r, kb, ldb);
-    // L21 = B21 L11^-T
-    GEP_CHECK(dgemm(h, 'N', 'T', 'F', n2, r, r, 1.0, P, ldb, Dk, NB, 0.0, tmp, n2, engine));
-    GEP_CHECK(copy_matrix(h, n2, r, tmp, n2, P, ldb));
-    // B22 -= L21 L21^T (lower triangle)
-    GEP_CHECK(dgemm(h, 'N', 'T', 'L', n2, n2, r, -1.0, P, ldb, P, ldb, 1.0,
-                    B + GEP_IX(kb + r, kb + r, ldb), ldb, engine));
-  }
-  return GEP_OK;
+  return potrf_rec(h, 0, M, B, ldb, invD, tmp, engine);
 }
 
 // Eq. 5, "ScaLAPACK style": C = L^-1 (L^-1 A)^T with two blocked triangular solves.

@@ -22,10 +22,11 @@ namespace {
 constexpr int NBT = 64;     // panel width
 constexpr int SW = 64;      // SYMV strip width
 constexpr int SCH = 1024;   // SYMV rows per CTA
-constexpr int DCH = 2048;   // panel dot-product rows per CTA
+constexpr int DCH = 128;    // panel dot-product rows per CTA
 
 struct TWs {
-  double *Vp, *W, *y, *Pd, *Pt, *part, *part2;
+  double *Vp, *W, *y, *Pd, *Pt, *part, *part2, *WV, *tq;
+  float2* S2;  // float-pair copy of the trailing matrix (lower triangle) for the SYMVs
   int M, nblk, maxch, ndch;
 };
 
@@ -48,23 +49,6 @@ __device__ double block_sum(double v, double* red) {
   double r = red[0];
   __syncthreads();
   return r;
-}
-
-// Column c of the panel: C(r, c) -= sum_q V(r,q) W(c,q) + W(r,q) V(c,q), r >= c.
-__global__ void k_col_update(int M, int c, int i, double* C, int ldc, const double* __restrict__ Vp,
-                             const double* __restrict__ W, int ldp, const int* st) {
-  __shared__ double vc[NBT], wc[NBT];
-  if (status_bad(st)) return;
-  if (threadIdx.x < i) {
-    vc[threadIdx.x] = Vp[GEP_IX(c, threadIdx.x, ldp)];
-    wc[threadIdx.x] = W[GEP_IX(c, threadIdx.x, ldp)];
-  }
-  __syncthreads();
-  int r = c + blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= M) return;
-  double s = 0.0;
-  for (int q = 0; q < i; ++q) s = fma(Vp[GEP_IX(r, q, ldp)], wc[q], fma(W[GEP_IX(r, q, ldp)], vc[q], s));
-  C[GEP_IX(r, c, ldc)] -= s;
 }
 
 // Householder reflector of x = C(c+1:M, c):  H x = beta e_1, H = I - tau v v^T, v(0) = 1.
@@ -111,6 +95,136 @@ __global__ void k_last_diag(int M, const double* C, int ldc, double* d, const in
   d[M - 1] = C[GEP_IX(M - 1, M - 1, ldc)];
 }
 
+// ---- compensated single-precision arithmetic for the SYMV ----------------------
+// The SYMV needs two multiply-adds per matrix element; at this part's FP64 rate that
+// is ~3x slower than streaming the element from HBM.  The trailing matrix is kept
+// as an unevaluated float pair (hi, lo) with hi + lo = a to ~2^-48 relative, the
+// vector is split the same way, and every term is formed as an exact product
+// (FMA error term) plus the two cross terms, summed with TwoSum, so each partial
+// sum carries ~46 significant bits and the kernel stays bound by memory.
+struct ff {
+  float h, l;
+};
+
+__device__ __forceinline__ ff ff_split(double x) {
+  float h = (float)x;
+  float l = (float)(x - (double)h);
+  return {h, l};
+}
+
+// s += a * v (a, v float pairs), TwoSum on the leading parts.
+__device__ __forceinline__ void ff_madd(ff& s, float ah, float al, float vh, float vl) {
+  float p = ah * vh;
+  float e = fmaf(ah, vh, -p);
+  e = fmaf(ah, vl, e);
+  e = fmaf(al, vh, e);
+  float t = s.h + p;
+  float z = t - s.h;
+  float err = (s.h - (t - z)) + (p - z);
+  s.h = t;
+  s.l += err + e;
+}
+
+// Lower triangle of the n x n block at A (FP64) -> float pairs at S (same indexing).
+__global__ void k_to_ff(int n, const double* __restrict__ A, int lda, float2* __restrict__ S, int lds,
+                        const int* st) {
+  if (status_bad(st)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int j = blockIdx.y; j < n; j += gridDim.y) {
+    if (i < n && i >= j) {
+      double x = A[GEP_IX(i, j, lda)];
+      float h = (float)x;
+      S[GEP_IX(i, j, lds)] = make_float2(h, (float)(x - (double)h));
+    }
+  }
+}
+
+// Same partial-product scheme as k_symv_partial below, on the float-pair matrix.
+__global__ void __launch_bounds__(256) k_symv_partial_ff(int n, const float2* __restrict__ A, int lda,
+                                                         const double* __restrict__ v, double* __restrict__ Pd,
+                                                         double* __restrict__ Pt, int maxch, const int* st) {
+  __shared__ float vsh[SW], vsl[SW];
+  __shared__ double dsum[4][SCH];
+  __shared__ double tsum[4][2][16];
+  if (status_bad(st)) return;
+  int jb = blockIdx.x, ch = blockIdx.y;
+  int c0 = jb * SW;
+  int R0 = c0 + ch * SCH;
+  if (R0 >= n) return;
+  int rl = threadIdx.x & 63, cq = threadIdx.x >> 6;
+  if (threadIdx.x < SW) {
+    ff t = ff_split((c0 + threadIdx.x < n) ? v[c0 + threadIdx.x] : 0.0);
+    vsh[threadIdx.x] = t.h;
+    vsl[threadIdx.x] = t.l;
+  }
+  __syncthreads();
+  int cbase = c0 + cq * 16;
+  int ncols = min(16, n - cbase);
+  ff acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = {0.f, 0.f};
+  int rend = min(n, R0 + SCH);
+  for (int p = 0; p < SCH / 64; ++p) {
+    int r = R0 + p * 64 + rl;
+    ff dir = {0.f, 0.f};
+    if (r < rend && ncols > 0) {
+      ff vr = ff_split(v[r]);
+      const float2* arow = A + r;
+      if (r >= cbase + 16 && ncols == 16) {
+        // full quarter strictly below the diagonal: issue all 16 loads, then compute
+        float2 a[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) a[q] = __ldg(arow + (size_t)(cbase + q) * lda);
+        ff dir2 = {0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q < 16; q += 2) {
+          ff_madd(dir, a[q].x, a[q].y, vsh[cq * 16 + q], vsl[cq * 16 + q]);
+          ff_madd(dir2, a[q + 1].x, a[q + 1].y, vsh[cq * 16 + q + 1], vsl[cq * 16 + q + 1]);
+          ff_madd(acc[q], a[q].x, a[q].y, vr.h, vr.l);
+          ff_madd(acc[q + 1], a[q + 1].x, a[q + 1].y, vr.h, vr.l);
+        }
+        ff_madd(dir, dir2.h, 0.f, 1.f, 0.f);
+        dir.l += dir2.l;
+      } else if (r >= cbase + 16) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          if (q < ncols) {
+            float2 a = arow[(size_t)(cbase + q) * lda];
+            ff_madd(dir, a.x, a.y, vsh[cq * 16 + q], vsl[cq * 16 + q]);
+            ff_madd(acc[q], a.x, a.y, vr.h, vr.l);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          int col = cbase + q;
+          if (q < ncols && r >= col) {
+            float2 a = arow[(size_t)col * lda];
+            ff_madd(dir, a.x, a.y, vsh[cq * 16 + q], vsl[cq * 16 + q]);
+            if (r > col) ff_madd(acc[q], a.x, a.y, vr.h, vr.l);
+          }
+        }
+      }
+    }
+    dsum[cq][p * 64 + rl] = (double)dir.h + (double)dir.l;
+  }
+  int lane = threadIdx.x & 31, wq = (threadIdx.x >> 5) & 1;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    double s = warp_sum((double)acc[q].h + (double)acc[q].l);
+    if (lane == 0) tsum[cq][wq][q] = s;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < SCH; t += blockDim.x) {
+    int r = R0 + t;
+    if (r < rend) Pd[(size_t)jb * n + r] = (dsum[0][t] + dsum[1][t]) + (dsum[2][t] + dsum[3][t]);
+  }
+  if (threadIdx.x < SW) {
+    int q4 = threadIdx.x >> 4, q = threadIdx.x & 15;
+    Pt[((size_t)jb * maxch + ch) * SW + threadIdx.x] = tsum[q4][0][q] + tsum[q4][1][q];
+  }
+}
+
 // Partial products of the symmetric SYMV y = A v over strip jb (columns 64 jb ..),
 // rows [R0, R0 + SCH) of the lower triangle.  256 threads = 64 row lanes x 4 column
 // quarters of 16 columns.  Direct terms A(r,c) v(c) (r >= c) go to Pd[jb][r];
@@ -141,7 +255,16 @@ __global__ void __launch_bounds__(256) k_symv_partial(int n, const double* __res
     if (r < rend && ncols > 0) {
       double vr = v[r];
       const double* arow = A + r;
-      if (r >= cbase + 16) {  // strictly below every column of this quarter
+      if (r >= cbase + 16 && ncols == 16) {  // full quarter below the diagonal: loads first
+        double a[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) a[q] = __ldg(arow + (size_t)(cbase + q) * lda);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          dir = fma(a[q], vs[cq * 16 + q], dir);
+          acc[q] = fma(a[q], vr, acc[q]);
+        }
+      } else if (r >= cbase + 16) {  // strictly below every column of this quarter
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           if (q < ncols) {
@@ -182,21 +305,6 @@ __global__ void __launch_bounds__(256) k_symv_partial(int n, const double* __res
   }
 }
 
-// y(r) = sum_{jb <= r/64} Pd[jb][r] + sum_ch Pt[r/64][ch][r%64]
-__global__ void k_symv_reduce(int n, const double* __restrict__ Pd, const double* __restrict__ Pt, int maxch,
-                              double* __restrict__ y, const int* st) {
-  if (status_bad(st)) return;
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  int jr = r / SW;
-  double s = 0.0;
-  for (int jb = 0; jb <= jr; ++jb) s += Pd[(size_t)jb * n + r];
-  int nch = (n - jr * SW + SCH - 1) / SCH;
-  double t = 0.0;
-  for (int ch = 0; ch < nch; ++ch) t += Pt[((size_t)jr * maxch + ch) * SW + (r - jr * SW)];
-  y[r] = s + t;
-}
-
 // Partial dots over rows [ch*DCH, ...) of t1 = W(:,0:i)^T v and t2 = V(:,0:i)^T v
 // (rows c+1 .. M-1 of the panel).  One warp per (matrix, column).
 __global__ void __launch_bounds__(256) k_panel_dots(int n, int i, const double* __restrict__ Vp,
@@ -216,26 +324,42 @@ __global__ void __launch_bounds__(256) k_panel_dots(int n, int i, const double* 
   }
 }
 
+// t[q] = sum over chunks of the panel dot partials (one CTA per q, fixed order).
+__global__ void __launch_bounds__(256) k_dots_reduce(int nch, const double* __restrict__ part,
+                                                     double* __restrict__ tq, const int* st) {
+  __shared__ double red[32];
+  if (status_bad(st)) return;
+  int q = blockIdx.x;
+  double s = 0.0;
+  for (int ch = threadIdx.x; ch < nch; ch += blockDim.x) s += part[(size_t)ch * 2 * NBT + q];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) tq[q] = s;
+}
+
+// y = A v from the SYMV partials (same fixed order as k_symv_reduce), then
 // w = tau (y - V t1 - W t2) on rows [blk*256, ...); also writes partial w.v.
-__global__ void __launch_bounds__(256) k_w_compute(int n, int i, int nch, const double* __restrict__ Vp,
+__global__ void __launch_bounds__(256) k_w_compute(int n, int i, const double* __restrict__ Vp,
                                                    const double* __restrict__ W, int ldp,
-                                                   const double* __restrict__ v, double* __restrict__ y,
-                                                   const double* __restrict__ part, const double* tau_c,
+                                                   const double* __restrict__ v, const double* __restrict__ Pd,
+                                                   const double* __restrict__ Pt, int maxch, double* __restrict__ y,
+                                                   const double* __restrict__ tq, const double* tau_c,
                                                    double* __restrict__ part2, const int* st) {
   __shared__ double t[2 * NBT];
   __shared__ double red[32];
   if (status_bad(st)) return;
-  if (threadIdx.x < 2 * i) {
-    double s = 0.0;
-    for (int ch = 0; ch < nch; ++ch) s += part[(size_t)ch * 2 * NBT + threadIdx.x];
-    t[threadIdx.x] = s;
-  }
+  if (threadIdx.x < 2 * i) t[threadIdx.x] = tq[threadIdx.x];
   __syncthreads();
   double tv = *tau_c;
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   double dotp = 0.0;
   if (r < n) {
-    double s = y[r];
+    int jr = r / SW;
+    double sd = 0.0;
+    for (int jb = 0; jb <= jr; ++jb) sd += Pd[(size_t)jb * n + r];
+    int nch = (n - jr * SW + SCH - 1) / SCH;
+    double stt = 0.0;
+    for (int ch = 0; ch < nch; ++ch) stt += Pt[((size_t)jr * maxch + ch) * SW + (r - jr * SW)];
+    double s = sd + stt;
     for (int q = 0; q < i; ++q) s -= Vp[GEP_IX(r, q, ldp)] * t[q] + W[GEP_IX(r, q, ldp)] * t[i + q];
     double w = tv * s;
     y[r] = w;
@@ -245,18 +369,39 @@ __global__ void __launch_bounds__(256) k_w_compute(int n, int i, int nch, const 
   if (threadIdx.x == 0) part2[blockIdx.x] = tot;
 }
 
-// alpha = -tau/2 (w.v);  W(:, i) = w + alpha v  (rows c+1 ..).
+// alpha = -tau/2 (w.v);  W(:, i) = w + alpha v  (rows c+1 ..).  With `next`, the same
+// kernel also applies the panel update to column c+1 (rows c+1 ..), which needs the
+// new W(:, i): every CTA recomputes W(c+1, i) from y(0), v(0) and alpha.
 __global__ void __launch_bounds__(256) k_w_finish(int n, int nblk, const double* __restrict__ y,
                                                   const double* __restrict__ v, const double* __restrict__ part2,
-                                                  const double* tau_c, double* __restrict__ Wi, const int* st) {
+                                                  const double* tau_c, int c, int i, int next, double* C, int ldc,
+                                                  const double* __restrict__ Vp, double* __restrict__ W, int ldp,
+                                                  const int* st) {
   __shared__ double red[32];
+  __shared__ double vc[NBT], wc[NBT];
   if (status_bad(st)) return;
   double s = 0.0;
   for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part2[b];
   double dot = block_sum(s, red);
   double alpha = -0.5 * (*tau_c) * dot;
+  if (next && threadIdx.x <= i) {
+    int q = threadIdx.x;
+    vc[q] = Vp[GEP_IX(c + 1, q, ldp)];
+    wc[q] = (q < i) ? W[GEP_IX(c + 1, q, ldp)] : fma(alpha, v[0], y[0]);
+  }
+  __syncthreads();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < n) Wi[r] = fma(alpha, v[r], y[r]);
+  if (r >= n) return;
+  double wnew = fma(alpha, v[r], y[r]);
+  W[GEP_IX(c + 1 + r, i, ldp)] = wnew;
+  if (next) {
+    int R = c + 1 + r;
+    double sum = 0.0;
+    for (int q = 0; q < i; ++q)
+      sum = fma(Vp[GEP_IX(R, q, ldp)], wc[q], fma(W[GEP_IX(R, q, ldp)], vc[q], sum));
+    sum = fma(Vp[GEP_IX(R, i, ldp)], wc[i], fma(wnew, vc[i], sum));
+    C[GEP_IX(R, c + 1, ldc)] -= sum;
+  }
 }
 
 TWs carve(double* ws, int M) {
@@ -274,6 +419,9 @@ TWs carve(double* ws, int M) {
   t.Pt = take((size_t)t.nblk * t.maxch * SW);
   t.part = take((size_t)t.ndch * 2 * NBT);
   t.part2 = take((size_t)(M + 255) / 256 + 1);
+  t.WV = take((size_t)M * 2 * NBT);
+  t.S2 = (float2*)take((size_t)M * M);
+  t.tq = take((size_t)2 * NBT);
   return t;
 }
 
@@ -283,7 +431,7 @@ size_t tridiag_ws_elems(int M) {
   size_t nblk = (M + SW - 1) / SW, maxch = (M + SCH - 1) / SCH, ndch = (M + DCH - 1) / DCH;
   auto r = [](size_t n) { return (n + 31) & ~(size_t)31; };
   return r((size_t)M * NBT) * 2 + r(M) + r(nblk * M) + r(nblk * maxch * SW) + r(ndch * 2 * NBT) +
-         r((M + 255) / 256 + 1);
+         r((M + 255) / 256 + 1) + r((size_t)M * 2 * NBT) + r((size_t)M * M) + r(2 * NBT);
 }
 
 int tridiag_1stage(gep_handle_t h, int M, double* C, int ldc, double* d, double* e, double* tau,
@@ -294,15 +442,20 @@ int tridiag_1stage(gep_handle_t h, int M, double* C, int ldc, double* d, double*
   const int ldp = M;
   cudaStream_t s = h->stream;
   const int* st = h->d_status;
+  // FP64 engine: plain FP64 SYMVs.  Tensor-core engines: compensated float-pair SYMVs.
+  const bool pairs = engine != GEP_PREC_FP64;
   for (int j0 = 0; j0 < M; j0 += NBT) {
     int nbp = min(NBT, M - j0);
     int done = 0;
+    if (pairs && M - j0 > 1) {
+      int nt = M - j0;
+      dim3 g((nt + 255) / 256, nt < 65535 ? nt : 65535);
+      k_to_ff<<<g, 256, 0, s>>>(nt, C + GEP_IX(j0, j0, ldc), ldc, t.S2 + GEP_IX(j0, j0, M), M, st);
+      GEP_CHECK(check_launch(h));
+    }
     for (int i = 0; i < nbp; ++i) {
       int c = j0 + i;
-      if (i > 0) {
-        k_col_update<<<(M - c + 255) / 256, 256, 0, s>>>(M, c, i, C, ldc, t.Vp + j0 * 0, t.W, ldp, st);
-        GEP_CHECK(check_launch(h));
-      }
+      // (columns i > 0 of the panel were already updated by the previous column's k_w_finish)
       if (c == M - 1) {
         k_last_diag<<<1, 1, 0, s>>>(M, C, ldc, d, st);
         GEP_CHECK(check_launch(h));
@@ -315,20 +468,26 @@ int tridiag_1stage(gep_handle_t h, int M, double* C, int ldc, double* d, double*
       const double* v = t.Vp + GEP_IX(c + 1, i, ldp);
       const double* A = C + GEP_IX(c + 1, c + 1, ldc);
       int nblk = (n + SW - 1) / SW, maxch = (n + SCH - 1) / SCH;
-      k_symv_partial<<<dim3(nblk, maxch), 256, 0, s>>>(n, A, ldc, v, t.Pd, t.Pt, maxch, st);
-      GEP_CHECK(check_launch(h));
-      k_symv_reduce<<<(n + 255) / 256, 256, 0, s>>>(n, t.Pd, t.Pt, maxch, t.y, st);
+      if (pairs)
+        k_symv_partial_ff<<<dim3(nblk, maxch), 256, 0, s>>>(n, t.S2 + GEP_IX(c + 1, c + 1, M), M, v, t.Pd, t.Pt,
+                                                            maxch, st);
+      else
+        k_symv_partial<<<dim3(nblk, maxch), 256, 0, s>>>(n, A, ldc, v, t.Pd, t.Pt, maxch, st);
       GEP_CHECK(check_launch(h));
       int ndch = (n + DCH - 1) / DCH;
       if (i > 0) {
         k_panel_dots<<<ndch, 256, 0, s>>>(n, i, t.Vp + (c + 1), t.W + (c + 1), ldp, v, t.part, st);
         GEP_CHECK(check_launch(h));
+        k_dots_reduce<<<2 * i, 256, 0, s>>>(ndch, t.part, t.tq, st);
+        GEP_CHECK(check_launch(h));
       }
       int nb256 = (n + 255) / 256;
-      k_w_compute<<<nb256, 256, 0, s>>>(n, i, ndch, t.Vp + (c + 1), t.W + (c + 1), ldp, v, t.y, t.part,
-                                        tau + c, t.part2, st);
+      k_w_compute<<<nb256, 256, 0, s>>>(n, i, t.Vp + (c + 1), t.W + (c + 1), ldp, v, t.Pd, t.Pt, maxch, t.y,
+                                        t.tq, tau + c, t.part2, st);
       GEP_CHECK(check_launch(h));
-      k_w_finish<<<nb256, 256, 0, s>>>(n, nb256, t.y, v, t.part2, tau + c, t.W + GEP_IX(c + 1, i, ldp), st);
+      int next = (i + 1 < nbp) ? 1 : 0;
+      k_w_finish<<<nb256, 256, 0, s>>>(n, nb256, t.y, v, t.part2, tau + c, c, i, next, C, ldc, t.Vp, t.W, ldp,
+                                       st);
       GEP_CHECK(check_launch(h));
     }
     if (done) break;
@@ -336,10 +495,18 @@ int tridiag_1stage(gep_handle_t h, int M, double* C, int ldc, double* d, double*
     int n2 = M - jn;
     if (n2 > 0) {
       // A(jn:, jn:) -= V W^T + W V^T on the lower triangle
-      GEP_CHECK(dgemm(h, 'N', 'T', 'L', n2, n2, nbp, -1.0, t.Vp + jn, ldp, t.W + jn, ldp, 1.0,
-                      C + GEP_IX(jn, jn, ldc), ldc, engine));
-      GEP_CHECK(dgemm(h, 'N', 'T', 'L', n2, n2, nbp, -1.0, t.W + jn, ldp, t.Vp + jn, ldp, 1.0,
-                      C + GEP_IX(jn, jn, ldc), ldc, engine));
+      if (nbp == NBT) {
+        // one product of depth 2*NBT: [V W] [W V]^T (V and W are adjacent in the workspace)
+        GEP_CHECK(copy_matrix(h, n2, NBT, t.W + jn, ldp, t.WV + jn, ldp));
+        GEP_CHECK(copy_matrix(h, n2, NBT, t.Vp + jn, ldp, t.WV + jn + (size_t)NBT * ldp, ldp));
+        GEP_CHECK(dgemm(h, 'N', 'T', 'L', n2, n2, 2 * NBT, -1.0, t.Vp + jn, ldp, t.WV + jn, ldp, 1.0,
+                        C + GEP_IX(jn, jn, ldc), ldc, engine));
+      } else {
+        GEP_CHECK(dgemm(h, 'N', 'T', 'L', n2, n2, nbp, -1.0, t.Vp + jn, ldp, t.W + jn, ldp, 1.0,
+                        C + GEP_IX(jn, jn, ldc), ldc, engine));
+        GEP_CHECK(dgemm(h, 'N', 'T', 'L', n2, n2, nbp, -1.0, t.W + jn, ldp, t.Vp + jn, ldp, 1.0,
+                        C + GEP_IX(jn, jn, ldc), ldc, engine));
+      }
     }
   }
   return GEP_OK;
