@@ -45,6 +45,7 @@ typedef struct gep_handle_s* gep_handle_t;
 #define GEP_ERR_TIMEOUT (-103)     /* a bounded device-side wait gave up            */
 #define GEP_ERR_HANDLE (-104)      /* NULL or destroyed handle                      */
 #define GEP_ERR_UNSUPPORTED (-105) /* option combination not implemented            */
+#define GEP_ERR_TOO_LARGE (-106)   /* exceeds the fixed scratch of gep_dgemm_emulated_noalloc */
 
 /* Reducer variants (section 3.1, "ScaLAPACK style" / "ELPA style"). */
 #define GEP_RED_TWOSIDED 0     /* C = L^-1 A L^-T by triangular solves, L^-1 never formed */
@@ -168,6 +169,29 @@ const char* gep_status_string(int code);
 int gep_dgemm(gep_handle_t h, char transa, char transb, char uplo, int m, int n, int k, double alpha,
               const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
               int engine);
+
+/* ---- allocation-free product (no counterpart in the paper) ---------------------
+ * For callers that cannot call cudaMalloc, e.g. a framework that owns the whole
+ * device-memory budget through its own pool, or a latency-critical loop that must
+ * not let a library grow its footprint or enter the allocator mid-run.
+ * Computes the same product as gep_dgemm(..., GEP_PREC_FP64_EMULATED) without a
+ * handle or workspace: its scratch (digit planes, exponents, a status word) is a
+ * fixed 64 MiB device array inside this library, which every GPU that loads the
+ * library keeps until the process exits.  The caller passes A, B, C (device memory)
+ * and the stream (a cudaStream_t as void*, NULL = legacy default stream).
+ *  - Sizes: requires 2*8*(m+n)*32 + 4*(m+n) bytes plus ~1.3 KB to fit in 64 MiB,
+ *    i.e. m + n <= 130,000 or so; larger problems return GEP_ERR_TOO_LARGE before
+ *    anything is enqueued.  Long K is processed in panels sized to the array.
+ *  - The first call on a device resolves the array's device address for that device
+ *    (cudaGetSymbolAddress with the caller's current device); make that first call
+ *    before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents; calls that
+ *    overlap on the GPU (other streams, other threads) race on it.  Serialise them.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * Returns 0, -i for an illegal argument i, GEP_ERR_TOO_LARGE or GEP_ERR_CUDA. */
+int gep_dgemm_emulated_noalloc(char transa, char transb, char uplo, int m, int n, int k, double alpha,
+                               const double* A, int lda, const double* B, int ldb, double beta, double* C,
+                               int ldc, void* stream);
 
 #ifdef __cplusplus
 }

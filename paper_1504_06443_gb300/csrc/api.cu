@@ -239,6 +239,7 @@ const char* gep_status_string(int code) {
     case GEP_ERR_TIMEOUT: return "a bounded device-side wait gave up";
     case GEP_ERR_HANDLE: return "invalid handle";
     case GEP_ERR_UNSUPPORTED: return "option combination not implemented";
+    case GEP_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of the allocation-free entry point";
     default: break;
   }
   if (code < 0 && code >= -20) return "illegal argument";

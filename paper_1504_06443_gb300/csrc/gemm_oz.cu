@@ -594,3 +594,69 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
 }
 
 }  // namespace gep
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the split-BF16 product (gep_dgemm_emulated_noalloc).
+//
+// Some callers cannot call cudaMalloc: a framework that owns the whole device-memory
+// budget through its own pool, or a latency-critical loop that must not let a
+// library grow its footprint or hit the allocator mid-run.  This entry point needs
+// neither a handle nor a workspace: the digit planes, row/column exponents and the
+// status word live in the fixed device array below, which every GPU that loads this
+// library holds until the process exits.  The product is the same as gep_dgemm with
+// GEP_PREC_FP64_EMULATED; only the K-panel length differs (it is chosen to fit the
+// array), so results agree to rounding.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[64u << 20];
+
+namespace {
+constexpr size_t kNoallocBytes = 64u << 20;
+constexpr int kNoallocMaxDevices = 64;
+void* g_noalloc_ptr[kNoallocMaxDevices] = {};
+int g_noalloc_ready[kNoallocMaxDevices] = {};
+}  // namespace
+
+extern "C" int gep_dgemm_emulated_noalloc(char transa, char transb, char uplo, int m, int n, int k, double alpha,
+                                          const double* A, int lda, const double* B, int ldb, double beta, double* C,
+                                          int ldc, void* stream) {
+  bool ta = (transa == 'T' || transa == 't'), tb = (transb == 'T' || transb == 't');
+  if (!ta && transa != 'N' && transa != 'n') return -1;
+  if (!tb && transb != 'N' && transb != 'n') return -2;
+  if (uplo != 'F' && uplo != 'f' && uplo != 'L' && uplo != 'l') return -3;
+  if (m < 0) return -4;
+  if (n < 0) return -5;
+  if (k < 0) return -6;
+  if (lda < (ta ? (k > 1 ? k : 1) : (m > 1 ? m : 1))) return -9;
+  if (ldb < (tb ? (n > 1 ? n : 1) : (k > 1 ? k : 1))) return -11;
+  if (ldc < (m > 1 ? m : 1)) return -14;
+  // The array holds a 256-byte status block, then the planes of a K panel of at least
+  // 32 (8 planes x 2 bytes x (m + n) x 32) and the (m + n) exponents.
+  const size_t status_bytes = 256;
+  const size_t need_min = status_bytes + gep::align256((size_t)8 * 2 * ((size_t)m + n) * 32) +
+                          gep::align256((size_t)4 * ((size_t)m + n)) + 1024;
+  if (need_min > kNoallocBytes) return GEP_ERR_TOO_LARGE;
+  if (m == 0 || n == 0) return GEP_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return GEP_ERR_CUDA;
+  if (!g_noalloc_ready[dev]) {  // first call on this device (the device is current here)
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      fprintf(stderr, "gep: cudaGetSymbolAddress of the no-allocation scratch failed: %s\n", cudaGetErrorString(e));
+      return GEP_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+    g_noalloc_ready[dev] = 1;
+  }
+  char* base = (char*)g_noalloc_ptr[dev];
+  gep_handle_s h;  // stack-only view: no events, no split-K buffer, no allocation
+  h.stream = (cudaStream_t)stream;
+  h.d_status = (int*)base;
+  h.eng_ws = base + status_bytes;
+  h.eng_bytes = kNoallocBytes - status_bytes;
+  cudaDeviceGetAttribute(&h.sm_count, cudaDevAttrMultiProcessorCount, dev);
+  // the status words must start at zero; the digit planes are fully rewritten per panel
+  if (cudaMemsetAsync(h.d_status, 0, status_bytes, h.stream) != cudaSuccess) return GEP_ERR_CUDA;
+  int rc = gep::dgemm_oz(&h, transa, transb, uplo, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 9);
+  h.magic = 0;
+  return rc;
+}
