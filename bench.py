@@ -196,8 +196,10 @@ def sampled_check(A, B, w, Y, ncols=64, seed=0):
     G = Ys.t() @ BY
     orth = (G - torch.eye(ncols, dtype=G.dtype, device=G.device)).abs().max().item()
     rq = ((Ys * AY).sum(0) / (Ys * BY).sum(0) - ws).abs().max().item()
-    return {"cols": ncols, "max_col_residual_over_normA_rms": res, "orth_max": orth, "rayleigh_minus_w_max": rq,
-            "ascending": bool((w[1:] >= w[:-1]).all().item())}
+    # ||A Y - B Y Lambda||_F / (||A||_F M), estimated from the sampled columns
+    res_ns = math.sqrt(M / ncols * float((R * R).sum().item())) / (A.norm().item() * M)
+    return {"cols": ncols, "residual_F_over_normF_M_est": res_ns, "max_col_residual_over_normA_rms": res,
+            "orth_max": orth, "rayleigh_minus_w_max": rq, "ascending": bool((w[1:] >= w[:-1]).all().item())}
 
 
 def main():

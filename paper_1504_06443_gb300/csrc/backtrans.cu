@@ -3,13 +3,16 @@
 // applied from the last panel to the first in compact-WY form,
 //     H_j ... H_{j+nb-1} = I - V T V^T    (T upper triangular, forward/columnwise),
 //     Z(j+1:, :) -= V (T (V^T Z(j+1:, :))),
-// so all O(M^3) work is three matrix products per panel.
+// so all O(M^3) work is three matrix products per panel.  Panels are NBB = 256
+// reflectors wide (the update product then has depth 256); their T factor is built
+// recursively, T = [T1, -T1 (V1^T V2) T2; 0, T2], from 64-wide leaves.
 #include "gep_internal.cuh"
 
 namespace gep {
 namespace {
 
-constexpr int NBB = 64;
+constexpr int NBB = 256;
+constexpr int LB = 64;  // leaf order of the T-factor recursion
 
 // Explicit V (rows j0+1 .. M-1, nb columns): unit entry at local row q, reflector below.
 __global__ void k_build_v(int rows, int nb, int j0, const double* __restrict__ C, int ldc,
@@ -26,19 +29,20 @@ __global__ void k_build_v(int rows, int nb, int j0, const double* __restrict__ C
 }
 
 // T factor from G = V^T V:  T(i,i) = tau_i,  T(0:i, i) = -tau_i T(0:i, 0:i) G(0:i, i).
-__global__ void k_larft(int nb, const double* __restrict__ G, const double* __restrict__ tau,
-                        double* __restrict__ T, const int* st) {
-  __shared__ double Ts[NBB][NBB + 1];
-  __shared__ double col[NBB];
+// (leaf, nb <= LB; G and T with leading dimensions ldg, ldt)
+__global__ void k_larft(int nb, const double* __restrict__ G, int ldg, const double* __restrict__ tau,
+                        double* __restrict__ T, int ldt, const int* st) {
+  __shared__ double Ts[LB][LB + 1];
+  __shared__ double col[LB];
   if (status_bad(st)) return;
   int t = threadIdx.x;
-  for (int idx = t; idx < NBB * NBB; idx += blockDim.x) Ts[idx % NBB][idx / NBB] = 0.0;
+  for (int idx = t; idx < LB * LB; idx += blockDim.x) Ts[idx % LB][idx / LB] = 0.0;
   __syncthreads();
   for (int i = 0; i < nb; ++i) {
     double ti = tau[i];
     if (t < i) {
       double s = 0.0;
-      for (int u = t; u < i; ++u) s = fma(Ts[t][u], G[GEP_IX(u, i, nb)], s);
+      for (int u = t; u < i; ++u) s = fma(Ts[t][u], G[GEP_IX(u, i, ldg)], s);
       col[t] = -ti * s;
     }
     __syncthreads();
@@ -46,14 +50,31 @@ __global__ void k_larft(int nb, const double* __restrict__ G, const double* __re
     if (t == 0) Ts[i][i] = ti;
     __syncthreads();
   }
-  for (int idx = t; idx < nb * nb; idx += blockDim.x) T[idx] = Ts[idx % nb][idx / nb];
+  for (int idx = t; idx < nb * nb; idx += blockDim.x) T[GEP_IX(idx % nb, idx / nb, ldt)] = Ts[idx % nb][idx / nb];
+}
+
+// T (nb x nb, upper) of the block reflector whose Gram matrix is G = V^T V.
+int larft_rec(gep_handle_t h, int nb, const double* G, int ldg, const double* tau, double* T, int ldt,
+              double* tmp) {
+  if (nb <= LB) {
+    k_larft<<<1, LB, 0, h->stream>>>(nb, G, ldg, tau, T, ldt, h->d_status);
+    return check_launch(h);
+  }
+  int n1 = ((nb / 2 + LB - 1) / LB) * LB, n2 = nb - n1;
+  GEP_CHECK(larft_rec(h, n1, G, ldg, tau, T, ldt, tmp));
+  GEP_CHECK(larft_rec(h, n2, G + GEP_IX(n1, n1, ldg), ldg, tau + n1, T + GEP_IX(n1, n1, ldt), ldt, tmp));
+  GEP_CHECK(set_matrix(h, n2, n1, 0.0, 0.0, T + n1, ldt));  // strictly lower block
+  // T12 = -T1 (G12 T2)
+  GEP_CHECK(dgemm_f64(h, 'N', 'N', 'F', n1, n2, n2, 1.0, G + GEP_IX(0, n1, ldg), ldg, T + GEP_IX(n1, n1, ldt), ldt,
+                      0.0, tmp, n1));
+  return dgemm_f64(h, 'N', 'N', 'F', n1, n2, n1, -1.0, T, ldt, tmp, n1, 0.0, T + GEP_IX(0, n1, ldt), ldt);
 }
 
 }  // namespace
 
 size_t backtransform_ws_elems(int M, int ncol) {
   auto r = [](size_t n) { return (n + 31) & ~(size_t)31; };
-  return r((size_t)M * NBB) + r((size_t)NBB * NBB) * 2 + r((size_t)NBB * (ncol > 0 ? ncol : 1)) * 2;
+  return r((size_t)M * NBB) + r((size_t)NBB * NBB) * 3 + r((size_t)NBB * (ncol > 0 ? ncol : 1)) * 2;
 }
 
 int backtransform_q(gep_handle_t h, int M, int ncol, const double* C, int ldc, const double* tau,
@@ -64,7 +85,8 @@ int backtransform_q(gep_handle_t h, int M, int ncol, const double* C, int ldc, c
   double* V = ws;
   double* G = V + r((size_t)M * NBB);
   double* T = G + r((size_t)NBB * NBB);
-  double* W1 = T + r((size_t)NBB * NBB);
+  double* Tt = T + r((size_t)NBB * NBB);  // recursion scratch
+  double* W1 = Tt + r((size_t)NBB * NBB);
   double* W2 = W1 + r((size_t)NBB * ncol);
   int nref = M - 1;  // reflectors exist for columns 0 .. M-2
   int last = ((nref - 1) / NBB) * NBB;
@@ -75,8 +97,7 @@ int backtransform_q(gep_handle_t h, int M, int ncol, const double* C, int ldc, c
     k_build_v<<<g, 256, 0, h->stream>>>(rows, nb, j0, C, ldc, V, h->d_status);
     GEP_CHECK(check_launch(h));
     GEP_CHECK(dgemm(h, 'T', 'N', 'F', nb, nb, rows, 1.0, V, rows, V, rows, 0.0, G, nb, engine));
-    k_larft<<<1, NBB, 0, h->stream>>>(nb, G, tau + j0, T, h->d_status);
-    GEP_CHECK(check_launch(h));
+    GEP_CHECK(larft_rec(h, nb, G, nb, tau + j0, T, nb, Tt));
     double* Zs = Z + (j0 + 1);
     // transposed products keep the long dimension (ncol) as the row dimension of
     // each product, so all three fill full tensor-core tiles:

@@ -106,10 +106,63 @@ struct ff {
   float h, l;
 };
 
+// x = h + l with h = x rounded to 24 significant bits and l = x - h (|l| <= 2^-25 |x|,
+// itself rounded to float), built from the IEEE bits with integer instructions (on
+// this part the float<->double conversions run on the slow FP64 pipe).  Values whose
+// exponent is outside a comfortable float range take the conversion path.
 __device__ __forceinline__ ff ff_split(double x) {
-  float h = (float)x;
-  float l = (float)(x - (double)h);
-  return {h, l};
+  long long b = __double_as_longlong(x);
+  int E = (int)((b >> 52) & 0x7FF);
+  if (E < 1023 - 70 || E > 1023 + 120) {
+    if (E == 0) return {0.f, 0.f};
+    float h = (float)x;
+    return {h, (float)(x - (double)h)};
+  }
+  unsigned sign = (unsigned)((unsigned long long)b >> 63);
+  long long m53 = (long long)(((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+  long long m24 = (m53 + (1ll << 28)) >> 29;       // rounded 24-bit significand (may carry to 2^24)
+  long long lo_int = m53 - (m24 << 29);            // |lo_int| <= 2^28, exact
+  unsigned hb;
+  if (m24 >> 24) hb = (sign << 31) | ((unsigned)(E - 1023 + 128) << 23);  // rounded up to 2^(E-1022)
+  else hb = (sign << 31) | ((unsigned)(E - 1023 + 127) << 23) | ((unsigned)m24 & 0x7FFFFFu);
+  float scale = __int_as_float((E - 1075 + 127) << 23);  // 2^(E-1075), a normal float here
+  float l = __ll2float_rn(lo_int) * scale;
+  return {__int_as_float((int)hb), sign ? -l : l};
+}
+
+// s += x (float pairs), TwoSum on the leading parts.
+__device__ __forceinline__ void ff_add(ff& s, ff x) {
+  float t = s.h + x.h;
+  float z = t - s.h;
+  float err = (s.h - (t - z)) + (x.h - z);
+  s.h = t;
+  s.l += err + x.l;
+}
+
+// s += x with both parts TwoSum'ed and the pair renormalised (accurate double-float
+// addition, relative error ~3 * 2^-48 per step): used where hundreds of partial sums
+// of one row are added, so the error does not grow with their number.
+__device__ __forceinline__ void ff_add_acc(ff& s, ff x) {
+  float hs = s.h + x.h;
+  float z = hs - s.h;
+  float eh = (s.h - (hs - z)) + (x.h - z);
+  float ls = s.l + x.l;
+  float z2 = ls - s.l;
+  float el = (s.l - (ls - z2)) + (x.l - z2);
+  eh += ls;
+  float h2 = hs + eh;
+  eh = eh - (h2 - hs);
+  eh += el;
+  s.h = h2 + eh;
+  s.l = eh - (s.h - h2);
+}
+
+__device__ __forceinline__ ff ff_warp_sum(ff v) {
+  for (int o = 16; o; o >>= 1) {
+    ff u = {__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+    ff_add_acc(v, u);
+  }
+  return v;
 }
 
 // s += a * v (a, v float pairs), TwoSum on the leading parts.
@@ -132,9 +185,8 @@ __global__ void k_to_ff(int n, const double* __restrict__ A, int lda, float2* __
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   for (int j = blockIdx.y; j < n; j += gridDim.y) {
     if (i < n && i >= j) {
-      double x = A[GEP_IX(i, j, lda)];
-      float h = (float)x;
-      S[GEP_IX(i, j, lds)] = make_float2(h, (float)(x - (double)h));
+      ff p = ff_split(A[GEP_IX(i, j, lda)]);
+      S[GEP_IX(i, j, lds)] = make_float2(p.h, p.l);
     }
   }
 }
@@ -144,8 +196,8 @@ __global__ void __launch_bounds__(256) k_symv_partial_ff(int n, const float2* __
                                                          const double* __restrict__ v, double* __restrict__ Pd,
                                                          double* __restrict__ Pt, int maxch, const int* st) {
   __shared__ float vsh[SW], vsl[SW];
-  __shared__ double dsum[4][SCH];
-  __shared__ double tsum[4][2][16];
+  __shared__ float2 dsum[4][SCH];
+  __shared__ float2 tsum[4][2][16];
   if (status_bad(st)) return;
   int jb = blockIdx.x, ch = blockIdx.y;
   int c0 = jb * SW;
@@ -206,22 +258,33 @@ __global__ void __launch_bounds__(256) k_symv_partial_ff(int n, const float2* __
         }
       }
     }
-    dsum[cq][p * 64 + rl] = (double)dir.h + (double)dir.l;
+    dsum[cq][p * 64 + rl] = make_float2(dir.h, dir.l);
   }
   int lane = threadIdx.x & 31, wq = (threadIdx.x >> 5) & 1;
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
-    double s = warp_sum((double)acc[q].h + (double)acc[q].l);
-    if (lane == 0) tsum[cq][wq][q] = s;
+    ff s = ff_warp_sum(acc[q]);
+    if (lane == 0) tsum[cq][wq][q] = make_float2(s.h, s.l);
   }
   __syncthreads();
+  // partials stay float pairs; k_w_compute adds them up and converts once per row
+  float2* Pd2 = reinterpret_cast<float2*>(Pd);
+  float2* Pt2 = reinterpret_cast<float2*>(Pt);
   for (int t = threadIdx.x; t < SCH; t += blockDim.x) {
     int r = R0 + t;
-    if (r < rend) Pd[(size_t)jb * n + r] = (dsum[0][t] + dsum[1][t]) + (dsum[2][t] + dsum[3][t]);
+    if (r < rend) {
+      ff s = {dsum[0][t].x, dsum[0][t].y};
+      ff_add_acc(s, {dsum[1][t].x, dsum[1][t].y});
+      ff_add_acc(s, {dsum[2][t].x, dsum[2][t].y});
+      ff_add_acc(s, {dsum[3][t].x, dsum[3][t].y});
+      Pd2[(size_t)jb * n + r] = make_float2(s.h, s.l);
+    }
   }
   if (threadIdx.x < SW) {
     int q4 = threadIdx.x >> 4, q = threadIdx.x & 15;
-    Pt[((size_t)jb * maxch + ch) * SW + threadIdx.x] = tsum[q4][0][q] + tsum[q4][1][q];
+    ff s = {tsum[q4][0][q].x, tsum[q4][0][q].y};
+    ff_add_acc(s, {tsum[q4][1][q].x, tsum[q4][1][q].y});
+    Pt2[((size_t)jb * maxch + ch) * SW + threadIdx.x] = make_float2(s.h, s.l);
   }
 }
 
@@ -341,9 +404,9 @@ __global__ void __launch_bounds__(256) k_dots_reduce(int nch, const double* __re
 __global__ void __launch_bounds__(256) k_w_compute(int n, int i, const double* __restrict__ Vp,
                                                    const double* __restrict__ W, int ldp,
                                                    const double* __restrict__ v, const double* __restrict__ Pd,
-                                                   const double* __restrict__ Pt, int maxch, double* __restrict__ y,
-                                                   const double* __restrict__ tq, const double* tau_c,
-                                                   double* __restrict__ part2, const int* st) {
+                                                   const double* __restrict__ Pt, int maxch, int pairs,
+                                                   double* __restrict__ y, const double* __restrict__ tq,
+                                                   const double* tau_c, double* __restrict__ part2, const int* st) {
   __shared__ double t[2 * NBT];
   __shared__ double red[32];
   if (status_bad(st)) return;
@@ -354,12 +417,29 @@ __global__ void __launch_bounds__(256) k_w_compute(int n, int i, const double* _
   double dotp = 0.0;
   if (r < n) {
     int jr = r / SW;
-    double sd = 0.0;
-    for (int jb = 0; jb <= jr; ++jb) sd += Pd[(size_t)jb * n + r];
     int nch = (n - jr * SW + SCH - 1) / SCH;
-    double stt = 0.0;
-    for (int ch = 0; ch < nch; ++ch) stt += Pt[((size_t)jr * maxch + ch) * SW + (r - jr * SW)];
-    double s = sd + stt;
+    double s;
+    if (pairs) {  // float-pair partials from k_symv_partial_ff
+      const float2* Pd2 = reinterpret_cast<const float2*>(Pd);
+      const float2* Pt2 = reinterpret_cast<const float2*>(Pt);
+      ff sd = {0.f, 0.f}, stt = {0.f, 0.f};
+      for (int jb = 0; jb <= jr; ++jb) {
+        float2 p = Pd2[(size_t)jb * n + r];
+        ff_add_acc(sd, {p.x, p.y});
+      }
+      for (int ch = 0; ch < nch; ++ch) {
+        float2 p = Pt2[((size_t)jr * maxch + ch) * SW + (r - jr * SW)];
+        ff_add_acc(stt, {p.x, p.y});
+      }
+      ff_add_acc(sd, stt);
+      s = (double)sd.h + (double)sd.l;
+    } else {
+      double sd = 0.0;
+      for (int jb = 0; jb <= jr; ++jb) sd += Pd[(size_t)jb * n + r];
+      double stt = 0.0;
+      for (int ch = 0; ch < nch; ++ch) stt += Pt[((size_t)jr * maxch + ch) * SW + (r - jr * SW)];
+      s = sd + stt;
+    }
     for (int q = 0; q < i; ++q) s -= Vp[GEP_IX(r, q, ldp)] * t[q] + W[GEP_IX(r, q, ldp)] * t[i + q];
     double w = tv * s;
     y[r] = w;
@@ -482,8 +562,8 @@ int tridiag_1stage(gep_handle_t h, int M, double* C, int ldc, double* d, double*
         GEP_CHECK(check_launch(h));
       }
       int nb256 = (n + 255) / 256;
-      k_w_compute<<<nb256, 256, 0, s>>>(n, i, t.Vp + (c + 1), t.W + (c + 1), ldp, v, t.Pd, t.Pt, maxch, t.y,
-                                        t.tq, tau + c, t.part2, st);
+      k_w_compute<<<nb256, 256, 0, s>>>(n, i, t.Vp + (c + 1), t.W + (c + 1), ldp, v, t.Pd, t.Pt, maxch,
+                                        pairs ? 1 : 0, t.y, t.tq, tau + c, t.part2, st);
       GEP_CHECK(check_launch(h));
       int next = (i + 1 < nbp) ? 1 : 0;
       k_w_finish<<<nb256, 256, 0, s>>>(n, nb256, t.y, v, t.part2, tau + c, c, i, next, C, ldc, t.Vp, t.W, ldp,
