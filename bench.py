@@ -36,7 +36,7 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--M", type=int, default=32768)
     p.add_argument("--seed", type=int, default=0)
-    p.add_argument("--precision", default="fp64_emulated", choices=["fp64_emulated", "fp64"])
+    p.add_argument("--precision", default="fp64_emulated", choices=["fp64_emulated", "fp64", "mixed_refined"])
     p.add_argument("--reducer", default="twosided", choices=["twosided", "explicit_inv"])
     p.add_argument("--cpu-sample-M", type=int, default=2048)
     p.add_argument("--no-e2e", action="store_true")
@@ -44,7 +44,165 @@ def parse():
     p.add_argument("--no-check", action="store_true")
     p.add_argument("--gemm", type=int, nargs=3, metavar=("m", "n", "k"),
                    help="time only the split-BF16 product engine on an m x n x k product (profiling aid)")
+    p.add_argument("--compare-mixed", action="store_true",
+                   help="mixed+refined vs FP64-accurate solve of the same pencil (default M=16384)")
+    p.add_argument("--batched", action="store_true",
+                   help="512 tight-binding pencils, orders log-uniform in [64, 2048], one captured graph")
+    p.add_argument("--batch-count", type=int, default=512)
+    p.add_argument("--adjoint", action="store_true",
+                   help="forward+adjoint of sum(lambda_occ) + <W, P> at M=4096 with central differences")
+    p.add_argument("--fd-dirs", type=int, default=8)
     return p.parse_args()
+
+
+def _median_clock(clk):
+    return clk.stop()
+
+
+def run_compare_mixed(a):
+    import torch
+    import gep_inputs as gi
+    from paper_1504_06443_gb300 import build as gbuild
+    import paper_1504_06443_gb300 as gep
+    gbuild.build()
+    M = a.M if a.M != 32768 else 16384
+    tb = gi.tight_binding(M, a.seed)
+    A = torch.as_tensor(tb["A"]).cuda()
+    B = torch.as_tensor(tb["B"]).cuda()
+    out = {"metric": "mixed+refined vs FP64-accurate GEP solve time", "M": M, "unit": "s",
+           "higher_is_better": False, "data": "synthetic", "config": {"workload": f"tight-binding GEP M={M}"}}
+    res = {}
+    for prec in ("fp64_emulated", "mixed_refined"):
+        h = gep.Handle()
+        for _ in range(max(1, a.warmup)):
+            w, Y, info = gep.solve(A, B, precision=prec, timers=True, handle=h)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.steps):
+            w, Y, info = gep.solve(A, B, precision=prec, timers=True, handle=h)
+        e1.record()
+        torch.cuda.synchronize()
+        res[prec] = {"s": e0.elapsed_time(e1) / a.steps / 1e3, "info": info,
+                     "stage_ms": [round(x, 1) for x in h.stage_times()],
+                     "check": sampled_check(A, B, w, Y, 64, a.seed)}
+        res[prec]["w"] = w.clone()
+        h.close()
+    nA = float(torch.linalg.eigvalsh(A).abs().max().item()) if M <= 8192 else float(A.abs().sum(1).max().item())
+    dw = float((res["mixed_refined"]["w"] - res["fp64_emulated"]["w"]).abs().max().item())
+    for r in res.values():
+        r.pop("w")
+    out.update({"fp64": res["fp64_emulated"], "mixed_refined": res["mixed_refined"],
+                "max_abs_dlambda_over_normA": dw / nA,
+                "normA_kind": "2-norm" if M <= 8192 else "row-sum bound (>= 2-norm)",
+                "speedup_mixed_vs_fp64": res["fp64_emulated"]["s"] / res["mixed_refined"]["s"]})
+    print(json.dumps(out), flush=True)
+
+
+def run_batched(a):
+    import time
+    import torch
+    import gep_inputs as gi
+    from paper_1504_06443_gb300 import build as gbuild
+    import paper_1504_06443_gb300 as gep
+    gbuild.build()
+    orders = gi.batch_orders(a.batch_count, seed=1000)
+    t0 = time.time()
+    As, Bs = [], []
+    for i, M in enumerate(orders):
+        tb = gi.tight_binding(M, 1000 + i)
+        As.append(torch.as_tensor(tb["A"]).cuda())
+        Bs.append(torch.as_tensor(tb["B"]).cuda())
+    gen_s = time.time() - t0
+    reps = [next(i for i, M in enumerate(orders) if gep._bucket(M) == b) for b in sorted({gep._bucket(M) for M in orders})]
+    tuner = gep.Autotuner()
+    choice = tuner.tune([As[i] for i in reps], [Bs[i] for i in reps], reps=1)
+    precs = [tuner.precision_for(M) for M in orders]
+    flops = sum(7.0 * float(M) ** 3 for M in orders)
+    # looping single solves on one stream (baseline)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for A, B, p in zip(As, Bs, precs):
+        gep.solve(A, B, precision=p)
+    e1.record()
+    torch.cuda.synchronize()
+    loop_s = e0.elapsed_time(e1) / 1e3
+    bs = gep.BatchedSolver(As, Bs, nstreams=16, precisions=precs)
+    bs.capture()
+    for _ in range(a.warmup):
+        bs.replay()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.steps):
+        bs.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / a.steps / 1e3
+    info = bs.info()
+    out = {"metric": "batched GEP throughput (all eigenpairs)", "value": len(orders) / s, "unit": "GEPs/s",
+           "higher_is_better": True, "seconds_per_batch": s, "looping_single_solves_s": loop_s,
+           "speedup_vs_loop": loop_s / s, "fp64_equiv_tflops": flops / s / 1e12, "info": info,
+           "steps": a.steps, "warmup": a.warmup, "data": "synthetic", "dtype": "f64",
+           "config": {"workload": f"{len(orders)} tight-binding pencils, M log-uniform in [64, 2048]",
+                      "orders_min_max": [min(orders), max(orders)], "nstreams": 16, "graph": "one captured CUDA graph",
+                      "autotuned_engine_per_bucket": {str(k): v for k, v in choice.items()},
+                      "generator_s": round(gen_s, 1)}}
+    print(json.dumps(out), flush=True)
+
+
+def run_adjoint(a):
+    import numpy as np
+    import torch
+    import gep_inputs as gi
+    from paper_1504_06443_gb300 import build as gbuild
+    import paper_1504_06443_gb300 as gep
+    gbuild.build()
+    M = a.M if a.M != 32768 else 4096
+    n = M // 2
+    tb = gi.tight_binding(M, a.seed)
+    A = torch.as_tensor(tb["A"]).cuda().requires_grad_(True)
+    B = torch.as_tensor(tb["B"]).cuda().requires_grad_(True)
+    W = torch.as_tensor(gi.random_symmetric(M, 1)).cuda()
+
+    def loss_of(A_, B_):
+        w, P = gep.eigh_density(A_, B_, n)
+        return w[:n].sum() + (W * P).sum(), w
+
+    for _ in range(max(1, a.warmup)):
+        loss, w = loss_of(A, B)
+        gA, gB = torch.autograd.grad(loss, (A, B))
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record()
+    loss, w = loss_of(A, B)
+    e1.record()
+    gA, gB = torch.autograd.grad(loss, (A, B))
+    e2.record()
+    torch.cuda.synchronize()
+    gap = float((w[n] - w[n - 1]).item())
+    rng = np.random.default_rng(2)
+    h = 1e-6
+    errs = []
+    with torch.no_grad():
+        for _ in range(a.fd_dirs):
+            dA = rng.standard_normal((M, M)); dA = dA + dA.T
+            dB = rng.standard_normal((M, M)); dB = dB + dB.T
+            dA *= 1e-3 * np.linalg.norm(tb["A"]) / np.linalg.norm(dA)
+            dB *= 0.1 * 0.1 / np.linalg.norm(dB)
+            dAt, dBt = torch.as_tensor(dA).cuda(), torch.as_tensor(dB).cuda()
+            fp, _ = loss_of(A + h * dAt, B + h * dBt)
+            fm, _ = loss_of(A - h * dAt, B - h * dBt)
+            fd = (fp - fm).item() / (2 * h)
+            an = float((gA * dAt).sum() + (gB * dBt).sum())
+            errs.append(abs(fd - an) / max(1.0, abs(fd)))
+    out = {"metric": "differentiable GEP: forward + adjoint time", "M": M, "n_occ": n, "unit": "s",
+           "forward_s": e0.elapsed_time(e1) / 1e3, "backward_s": e1.elapsed_time(e2) / 1e3,
+           "value": e0.elapsed_time(e2) / 1e3, "higher_is_better": False, "homo_lumo_gap": gap,
+           "fd_directions": a.fd_dirs, "fd_h": h, "fd_max_rel_err": max(errs) if errs else None,
+           "data": "synthetic", "dtype": "f64",
+           "config": {"workload": f"tight-binding GEP M={M}, loss = sum_occ lambda + <W, Y_o Y_o^T>"}}
+    print(json.dumps(out), flush=True)
 
 
 def run_gemm(a):
@@ -210,6 +368,15 @@ def main():
     if a.gemm:
         run_gemm(a)
         return
+    if a.compare_mixed:
+        run_compare_mixed(a)
+        return
+    if a.batched:
+        run_batched(a)
+        return
+    if a.adjoint:
+        run_adjoint(a)
+        return
     if a.impl == "reference":
         if world > 1:
             import torch.distributed as dist
@@ -340,7 +507,7 @@ def main():
                            "l2": "inputs larger than L2 (8.6 GB per matrix at M=32768)",
                            "generator_s": round(gen_s, 2)},
                 "stage_ms": dict(zip(["R1_cholesky", "R2_reduce", "S1_tridiag", "S2_dc", "S3_back_q",
-                                      "R3_backsub"], [round(x, 2) for x in stages])),
+                                      "R3_backsub", "MP3_refine"], [round(x, 2) for x in stages])),
                 "info": info, "gpu_launches": int(launches),
                 "fp64_equiv_tflops_whole_solve": flops_alg / (ms_max * 1e-3) / 1e12,
                 "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "check": check}

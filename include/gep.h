@@ -69,9 +69,15 @@ typedef struct gep_options {
   int want_vectors; /* 1: eigenpairs (T_full); 0: eigenvalues only (T_evo)        */
   int overwrite;    /* 1: A and B may be destroyed by gep_solve (saves two copies) */
   int timers;       /* 1: record per-stage CUDA-event times (gep_get_stage_times) */
+  int refine_iters; /* GEP_PREC_MIXED_REFINED: FP64 refinement steps (0 = default, 2)  */
 } gep_options;
 
-/* Fills *o with the defaults: TWOSIDED, 1STAGE, b = 0, FP64, vectors, no overwrite, no timers. */
+/* Fills *o with the defaults: TWOSIDED, 1STAGE, b = 0, FP64, vectors, no overwrite, no timers.
+ * GEP_PREC_MIXED_REFINED (needs want_vectors = 1): every dense product of the solve runs
+ * on the FP32-grade split-BF16 engine and the SYMVs in FP32; FP64 stays in the diagonal
+ * blocks, the secular equations and deflation; then all eigenpairs are refined in FP64
+ * (B-Rayleigh quotients and the first-order correction X <- X (I + E) from S = X^T A X,
+ * R = X^T B X formed with FP64-accurate products). */
 void gep_default_options(gep_options* o);
 
 /* Creates a handle bound to `stream` (a cudaStream_t passed as void*; NULL = legacy
@@ -133,6 +139,39 @@ int gep_workspace_size_host(gep_handle_t h, int M, const gep_options* o, size_t*
 int gep_solve_host(gep_handle_t h, int M, const double* A, int lda, const double* B, int ldb,
                    double* w, double* Y, int ldy, const gep_options* o);
 
+/* ---- adjoint (reverse-mode derivative of Eq. 2) ---------------------------------
+ * For loss = sum_k lbar_k lambda_k + <W, P>, P = Y_o Y_o^T over the n_occ lowest
+ * eigenpairs, writes Abar = d loss / dA and Bbar = d loss / dB (full symmetric M x M,
+ * leading dimension ldab) from the output (w ascending, Y B-orthonormal) of gep_solve.
+ * First-order perturbation of Eq. 2: Abar = Y G Y^T, Bbar = Y H Y^T with G, H built from
+ * lbar, lambda and What = Y^T W Y on the occupied/virtual blocks (only occupied/virtual
+ * gaps are divided by).  lbar: M weights (NULL = 1 for occupied, 0 for virtual); W:
+ * symmetric M x M (lower read; NULL = no density term).  All pointers are device memory;
+ * the workspace must hold gep_adjoint_workspace_size bytes.  Dense products run on the
+ * FP64-accurate tensor-core engine. */
+int gep_adjoint_workspace_size(gep_handle_t h, int M, int n_occ, size_t* bytes);
+int gep_adjoint(gep_handle_t h, int M, int n_occ, const double* w, const double* Y, int ldy, const double* lbar,
+                const double* W, int ldw, double* Abar, double* Bbar, int ldab);
+
+/* ---- batched solves (many independent pencils of uneven order) -------------------
+ * Solves count pencils (A_i, B_i) of order M[i] with the workflow of gep_solve; host
+ * arrays of device pointers.  Work is spread over nstreams (1..64) concurrent child
+ * streams (largest M^3 first, each to the least loaded stream), forked from and joined
+ * back into the handle's stream with events, so the whole call can be captured into
+ * one CUDA graph (call it once outside capture first: that call creates the child
+ * streams and their status blocks).  precision[i] (may be NULL: o->precision for all)
+ * selects the product engine per pencil (the autotuned choice per size bucket).
+ * The workspace (gep_solve_batched_workspace_size) holds one solve workspace per
+ * stream, sized for the largest pencil that stream receives.  Numerical status of
+ * pencil i is not reported separately: gep_get_info covers the handle's own stream;
+ * check each child with gep_batched_info. */
+int gep_solve_batched_workspace_size(gep_handle_t h, int count, const int* M, const gep_options* o,
+                                     const int* precision, int nstreams, size_t* bytes);
+int gep_solve_batched(gep_handle_t h, int count, const int* M, double* const* A, double* const* B, double* const* w,
+                      double* const* Y, const gep_options* o, const int* precision, int nstreams);
+/* Synchronises and returns max over child streams of their numerical status. */
+int gep_batched_info(gep_handle_t h, int* info);
+
 /* Synchronises the stream and returns the numerical status in *info:
  *   0 ok; k in 1..M: leading minor k of B not positive definite (Eq. 4 failed);
  *   M + j: divide and conquer failed on a subproblem; GEP_ERR_NONFINITE / GEP_ERR_TIMEOUT. */
@@ -142,8 +181,9 @@ int gep_reset_info(gep_handle_t h);
 /* Per-stage times (ms) of the last gep_solve with o->timers = 1:
  * t[0] Cholesky (R1), t[1] reduction (R2), t[2] tridiagonalisation (TRD/BAND),
  * t[3] tridiagonal eigensolver (D&C), t[4] Householder back-transform (BACK),
- * t[5] back-substitution (R5 / Eq. 6).  Synchronises. */
-int gep_get_stage_times(gep_handle_t h, double t[6]);
+ * t[5] back-substitution (R5 / Eq. 6), t[6] FP64 refinement (mixed precision only, else ~0).
+ * Synchronises. */
+int gep_get_stage_times(gep_handle_t h, double t[7]);
 
 /* Number of kernels the library launched since gep_create / last reset. */
 long long gep_launch_count(gep_handle_t h, int reset);

@@ -44,7 +44,7 @@ class GepError(RuntimeError):
 class GepOptions(ctypes.Structure):
     _fields_ = [("reducer", ctypes.c_int), ("sep", ctypes.c_int), ("bandwidth", ctypes.c_int),
                 ("precision", ctypes.c_int), ("want_vectors", ctypes.c_int), ("overwrite", ctypes.c_int),
-                ("timers", ctypes.c_int)]
+                ("timers", ctypes.c_int), ("refine_iters", ctypes.c_int)]
 
 
 _lib = None
@@ -93,6 +93,12 @@ def load():
             "gep_profile_read": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D),
                                       ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), _I]),
             "gep_status_string": (ctypes.c_char_p, [_I]),
+            "gep_adjoint_workspace_size": (_I, [_P, _I, _I, ctypes.POINTER(_SZ)]),
+            "gep_adjoint": (_I, [_P, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I]),
+            "gep_solve_batched_workspace_size": (_I, [_P, _I, _P, ctypes.POINTER(GepOptions), _P, _I,
+                                                     ctypes.POINTER(_SZ)]),
+            "gep_solve_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(GepOptions), _P, _I]),
+            "gep_batched_info": (_I, [_P, ctypes.POINTER(_I)]),
             "gep_dgemm": (_I, [_P, ctypes.c_char, ctypes.c_char, ctypes.c_char, _I, _I, _I, _D, _P, _I, _P, _I,
                                _D, _P, _I, _I]),
         }
@@ -184,7 +190,7 @@ class Handle:
         _check(self.lib.gep_reset_info(self.h), "gep_reset_info")
 
     def stage_times(self):
-        t = (_D * 6)()
+        t = (_D * 7)()
         _check(self.lib.gep_get_stage_times(self.h, t), "gep_get_stage_times")
         return list(t)
 
@@ -392,3 +398,180 @@ def dgemm(A, B, transa="N", transb="N", alpha=1.0, beta=0.0, C=None, uplo="F", e
     _check(h.lib.gep_dgemm(h.h, transa.encode(), transb.encode(), uplo.encode(), m, n, k, float(alpha), _ptr(Ac),
                            _ld(Ac), _ptr(Bc), _ld(Bc), float(beta), _ptr(Cc), _ld(Cc), _PRECS[engine]), "gep_dgemm")
     return Cc
+
+
+# ------------------------------------------------------------------ adjoint
+
+def adjoint(w, Y, n_occ, lbar=None, W=None, handle=None):
+    """(Abar, Bbar) of loss = sum_k lbar_k lambda_k + <W, Y_o Y_o^T> (gep_adjoint).
+
+    w: eigenvalues ascending, Y: B-orthonormal eigenvectors (both from solve);
+    lbar: M weights (None = 1 on the n_occ occupied, 0 elsewhere); W: symmetric or None."""
+    torch = _torch()
+    h = handle or default_handle()
+    M = int(w.shape[0])
+    Yc = colmajor(Y)
+    ww = w.to(torch.float64).contiguous()
+    lb = None if lbar is None else lbar.to(torch.float64).contiguous()
+    Wc = None if W is None else colmajor(W)
+    Ab = torch.empty((M, M), dtype=torch.float64, device=w.device).t()
+    Bb = torch.empty((M, M), dtype=torch.float64, device=w.device).t()
+    n = _SZ()
+    _check(h.lib.gep_adjoint_workspace_size(h.h, M, int(n_occ), ctypes.byref(n)), "gep_adjoint_workspace_size")
+    h.ensure_workspace(n.value)
+    _check(h.lib.gep_adjoint(h.h, M, int(n_occ), _ptr(ww), _ptr(Yc), _ld(Yc), _ptr(lb), _ptr(Wc),
+                             _ld(Wc) if Wc is not None else max(1, M), _ptr(Ab), _ptr(Bb), max(1, M)), "gep_adjoint")
+    return Ab, Bb
+
+
+def _autograd_function():
+    torch = _torch()
+
+    class GEPDensity(torch.autograd.Function):
+        """(lambda, P) = eigenvalues and occupied density matrix P = Y_o Y_o^T of the pencil
+        (A, B); backward by the hand-written adjoint (no eigenvectors of the perturbation
+        are stored, only w and Y of the forward solve)."""
+
+        @staticmethod
+        def forward(ctx, A, B, n_occ, precision="fp64_emulated"):
+            w, Y, info = solve(A.detach(), B.detach(), precision=precision)
+            if info != 0:
+                raise GepError(info, "gep_solve (forward)")
+            Yc = colmajor(Y)
+            Yo = Yc[:, :n_occ]
+            P = dgemm(Yo, Yo, "N", "T", engine=precision if precision != "mixed_refined" else "fp64_emulated")
+            ctx.save_for_backward(w, Yc)
+            ctx.n_occ = int(n_occ)
+            return w, P.contiguous()
+
+        @staticmethod
+        def backward(ctx, gw, gP):
+            w, Yc = ctx.saved_tensors
+            lbar = None if gw is None else gw.contiguous()
+            if lbar is None:
+                lbar = torch.zeros_like(w)
+            W = None if gP is None else 0.5 * (gP + gP.t())
+            Ab, Bb = adjoint(w, Yc, ctx.n_occ, lbar, W)
+            return Ab.contiguous(), Bb.contiguous(), None, None
+
+    return GEPDensity
+
+
+_GEPDensity = None
+
+
+def eigh_density(A, B, n_occ, precision="fp64_emulated"):
+    """Differentiable (lambda, P = Y_o Y_o^T) of the pencil (A, B)."""
+    global _GEPDensity
+    if _GEPDensity is None:
+        _GEPDensity = _autograd_function()
+    return _GEPDensity.apply(A, B, n_occ, precision)
+
+
+# ------------------------------------------------------------------ batched
+
+SIZE_BUCKETS = (128, 256, 512, 1024, 2048, 4096)
+
+
+def _bucket(M):
+    for b in SIZE_BUCKETS:
+        if M <= b:
+            return b
+    return SIZE_BUCKETS[-1]
+
+
+class Autotuner:
+    """Per size bucket, the faster of the two FP64-accurate product engines (FP64 FMA
+    tiles or split-BF16 tensor-core tiles), timed on one pencil of the bucket."""
+
+    def __init__(self):
+        self.choice = {}
+
+    def tune(self, As, Bs, reps=2):
+        import time
+        torch = _torch()
+        for A, B in zip(As, Bs):
+            b = _bucket(int(A.shape[0]))
+            if b in self.choice:
+                continue
+            best, best_t = None, None
+            for eng in ("fp64", "fp64_emulated"):
+                solve(A, B, precision=eng)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    solve(A, B, precision=eng)
+                torch.cuda.synchronize()
+                t = (time.perf_counter() - t0) / reps
+                if best_t is None or t < best_t:
+                    best, best_t = eng, t
+            self.choice[b] = best
+        return self.choice
+
+    def precision_for(self, M):
+        return self.choice.get(_bucket(M), "fp64_emulated")
+
+
+class BatchedSolver:
+    """Many independent pencils (A_i, B_i) solved by gep_solve_batched over `nstreams`
+    concurrent streams; capture() records the whole batch into one CUDA graph that
+    replay() launches again (inputs are read from the same device buffers each time)."""
+
+    def __init__(self, As, Bs, nstreams=8, precision="fp64_emulated", precisions=None, handle=None):
+        torch = _torch()
+        self.h = handle or Handle()
+        self.count = len(As)
+        self.As = [a.contiguous() for a in As]
+        self.Bs = [b.contiguous() for b in Bs]
+        self.M = [int(a.shape[0]) for a in self.As]
+        dev = self.As[0].device
+        self.w = [torch.empty(m, dtype=torch.float64, device=dev) for m in self.M]
+        self.Yt = [torch.empty((m, m), dtype=torch.float64, device=dev) for m in self.M]
+        self.o = make_options(precision=precision)
+        self.nstreams = int(nstreams)
+        n = self.count
+        self._M = (ctypes.c_int * n)(*self.M)
+        self._A = (_P * n)(*[a.data_ptr() for a in self.As])
+        self._B = (_P * n)(*[b.data_ptr() for b in self.Bs])
+        self._w = (_P * n)(*[x.data_ptr() for x in self.w])
+        self._Y = (_P * n)(*[y.data_ptr() for y in self.Yt])
+        self._prec = None
+        if precisions is not None:
+            self._prec = (ctypes.c_int * n)(*[_PRECS[p] if isinstance(p, str) else int(p) for p in precisions])
+        nb = _SZ()
+        _check(self.h.lib.gep_solve_batched_workspace_size(self.h.h, n, self._M, ctypes.byref(self.o), self._prec,
+                                                            self.nstreams, ctypes.byref(nb)),
+               "gep_solve_batched_workspace_size")
+        self.h.ensure_workspace(nb.value)
+        self.graph = None
+
+    def run(self):
+        _check(self.h.lib.gep_solve_batched(self.h.h, self.count, self._M, self._A, self._B, self._w, self._Y,
+                                            ctypes.byref(self.o), self._prec, self.nstreams), "gep_solve_batched")
+
+    def capture(self):
+        torch = _torch()
+        self.run()  # eager first call creates the child streams outside the capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        _check(self.h.lib.gep_set_stream(self.h.h, ctypes.c_void_p(s.cuda_stream)), "gep_set_stream")
+        try:
+            with torch.cuda.graph(g, stream=s):
+                self.run()
+        finally:
+            _check(self.h.lib.gep_set_stream(self.h.h, ctypes.c_void_p(self.h.stream.cuda_stream)),
+                   "gep_set_stream")
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def info(self):
+        v = _I()
+        _check(self.h.lib.gep_batched_info(self.h.h, ctypes.byref(v)), "gep_batched_info")
+        return v.value
+
+    def results(self):
+        return [(w, Yt.t()) for w, Yt in zip(self.w, self.Yt)]

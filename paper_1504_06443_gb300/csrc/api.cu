@@ -15,7 +15,7 @@ constexpr int NB = 128;  // diagonal block order of the triangular kernels (tri.
 bool handle_ok(gep_handle_t h) { return h != nullptr && h->magic == 0x6e70; }
 
 struct SolveLayout {
-  size_t Cw, Lw, invD, vec, uni, eng, end;  // byte offsets
+  size_t Cw, Lw, invD, vec, uni, eng, af, end;  // byte offsets
   size_t uni_bytes, eng_bytes;
 };
 
@@ -34,7 +34,9 @@ size_t union_bytes(int M, const gep_options* o) {
   size_t dc = o->want_vectors ? dc_ws_bytes(M) : 0;
   size_t bt = o->want_vectors ? backtransform_ws_elems(M, M) * sizeof(double) : 0;
   size_t r3 = o->want_vectors ? (r256(tmpb) + (o->reducer == GEP_RED_EXPLICIT_INV ? r256(mm) : 0)) : 0;
+  size_t rf = (o->precision == GEP_PREC_MIXED_REFINED) ? r256(refine_ws_elems(M) * sizeof(double)) : 0;
   size_t u = red;
+  if (rf > u) u = rf;
   if (tri > u) u = tri;
   if (dc > u) u = dc;
   if (bt > u) u = bt;
@@ -56,6 +58,8 @@ SolveLayout layout(int M, const gep_options* o) {
   L.eng = off;
   L.eng_bytes = (o->precision == GEP_PREC_FP64) ? 0 : r256(oz_workspace_bytes(M, M, M));
   off += L.eng_bytes;
+  L.af = off;  // full symmetric A and B kept for the FP64 refinement
+  off += (o->precision == GEP_PREC_MIXED_REFINED) ? 2 * r256(mm) : 0;
   L.end = off;
   return L;
 }
@@ -64,7 +68,11 @@ int check_opts(const gep_options* o) {
   if (!o) return -1;
   if (o->reducer != GEP_RED_TWOSIDED && o->reducer != GEP_RED_EXPLICIT_INV) return GEP_ERR_UNSUPPORTED;
   if (o->sep != GEP_SEP_1STAGE) return GEP_ERR_UNSUPPORTED;
-  if (o->precision != GEP_PREC_FP64 && o->precision != GEP_PREC_FP64_EMULATED) return GEP_ERR_UNSUPPORTED;
+  if (o->precision != GEP_PREC_FP64 && o->precision != GEP_PREC_FP64_EMULATED &&
+      o->precision != GEP_PREC_MIXED_REFINED)
+    return GEP_ERR_UNSUPPORTED;
+  if (o->precision == GEP_PREC_MIXED_REFINED && !o->want_vectors) return GEP_ERR_UNSUPPORTED;
+  if (o->refine_iters < 0) return -10;
   return GEP_OK;
 }
 
@@ -114,6 +122,13 @@ int gep_create(gep_handle_t* out, void* stream) {
 int gep_destroy(gep_handle_t h) {
   if (!handle_ok(h)) return GEP_ERR_HANDLE;
   gep_profile_enable(h, 0);
+  for (int c = 0; c < h->nchild; ++c) {
+    gep_destroy(h->child[c]);
+    cudaEventDestroy(h->child_done[c]);
+    cudaStreamDestroy(h->child_stream[c]);
+  }
+  if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+  cudaFree(h->d_batch_info);
   for (int i = 0; i < 8; ++i) cudaEventDestroy(h->ev[i]);
   cudaFree(h->d_status);
   cudaFree(h->d_splitk);
@@ -217,12 +232,12 @@ int gep_profile_read(gep_handle_t h, double* ms, double* tensor_flops, double* f
   return GEP_OK;
 }
 
-int gep_get_stage_times(gep_handle_t h, double t[6]) {
+int gep_get_stage_times(gep_handle_t h, double t[7]) {
   if (!handle_ok(h)) return GEP_ERR_HANDLE;
   if (!t) return -2;
   if (!h->timers_recorded) return GEP_ERR_UNSUPPORTED;
-  GEP_CUDA(cudaEventSynchronize(h->ev[6]));
-  for (int i = 0; i < 6; ++i) {
+  GEP_CUDA(cudaEventSynchronize(h->ev[7]));
+  for (int i = 0; i < 7; ++i) {
     float ms = 0.f;
     GEP_CUDA(cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]));
     t[i] = ms;
@@ -413,6 +428,15 @@ int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, dou
   GEP_CHECK(reset_status(h));
   GEP_CHECK(scan_nonfinite(h, M, A, lda));
   GEP_CHECK(scan_nonfinite(h, M, B, ldb));
+  const bool mixed = o->precision == GEP_PREC_MIXED_REFINED;
+  double* Af = (double*)(base + Ly.af);
+  double* Bf = Af + align256((size_t)M * M * sizeof(double)) / sizeof(double);
+  if (mixed) {  // the refinement needs the original pencil, as full symmetric matrices
+    GEP_CHECK(copy_lower(h, M, A, lda, Af, M));
+    GEP_CHECK(symmetrize_lower(h, M, Af, M));
+    GEP_CHECK(copy_lower(h, M, B, ldb, Bf, M));
+    GEP_CHECK(symmetrize_lower(h, M, Bf, M));
+  }
   if (!o->overwrite) {
     GEP_CHECK(copy_lower(h, M, A, lda, Cw, ldcw));
     GEP_CHECK(copy_lower(h, M, B, ldb, Lw, ldlw));
@@ -438,6 +462,7 @@ int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, dou
     mark(h, o, 4);
     mark(h, o, 5);
     mark(h, o, 6);
+    mark(h, o, 7);
     h->timers_recorded = o->timers != 0;
     return GEP_OK;
   }
@@ -453,8 +478,168 @@ int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, dou
     GEP_CHECK(copy_matrix(h, M, M, T, M, Y, ldy));
   }
   mark(h, o, 6);
+  if (mixed) {
+    int iters = o->refine_iters > 0 ? o->refine_iters : 2;
+    GEP_CHECK(refine_eigenpairs(h, M, Af, Bf, Y, ldy, w, (double*)uni, iters, GEP_PREC_FP64_EMULATED));
+  }
+  mark(h, o, 7);
   GEP_CHECK(sign_convention(h, M, M, Y, ldy));
   h->timers_recorded = o->timers != 0;
+  return GEP_OK;
+}
+
+int gep_adjoint_workspace_size(gep_handle_t h, int M, int n_occ, size_t* bytes) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (M < 0) return -2;
+  if (n_occ < 0 || n_occ > M) return -3;
+  if (!bytes) return -4;
+  *bytes = r256(adjoint_ws_elems(M, n_occ) * sizeof(double)) + r256(oz_workspace_bytes(M, M, M));
+  return GEP_OK;
+}
+
+int gep_adjoint(gep_handle_t h, int M, int n_occ, const double* w, const double* Y, int ldy, const double* lbar,
+                const double* W, int ldw, double* Abar, double* Bbar, int ldab) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (M < 0) return -2;
+  if (n_occ < 0 || n_occ > M) return -3;
+  if (M > 0 && !w) return -4;
+  if (M > 0 && !Y) return -5;
+  if (ldy < (M > 1 ? M : 1)) return -6;
+  if (W && ldw < (M > 1 ? M : 1)) return -9;
+  if (M > 0 && (!Abar || !Bbar)) return -10;
+  if (ldab < (M > 1 ? M : 1)) return -12;
+  if (M == 0) return GEP_OK;
+  size_t need = 0;
+  GEP_CHECK(gep_adjoint_workspace_size(h, M, n_occ, &need));
+  if (h->ws == nullptr || h->ws_bytes < need) return GEP_ERR_ALLOC;
+  size_t main = r256(adjoint_ws_elems(M, n_occ) * sizeof(double));
+  h->eng_ws = h->ws + main;
+  h->eng_bytes = h->ws_bytes - main;
+  return adjoint(h, M, n_occ, w, Y, ldy, lbar, W, ldw, Abar, Bbar, ldab, (double*)h->ws, GEP_PREC_FP64_EMULATED);
+}
+
+// ---------------------------------------------------------------- batched solves
+namespace {
+
+constexpr int kMaxBatch = 4096;
+
+struct BatchPlan {
+  int ns;
+  int assign[kMaxBatch];
+  size_t need[64], off[64], total;
+};
+
+int make_plan(int count, const int* M, const gep_options* o, const int* prec, int nstreams, BatchPlan* p) {
+  if (count < 0 || count > kMaxBatch) return -2;
+  if (nstreams < 1 || nstreams > 64) return -7;
+  p->ns = nstreams < count ? nstreams : (count > 0 ? count : 1);
+  int order[kMaxBatch];
+  for (int i = 0; i < count; ++i) order[i] = i;
+  for (int a = 1; a < count; ++a) {  // stable insertion sort, M descending
+    int t = order[a], b = a - 1;
+    while (b >= 0 && M[order[b]] < M[t]) { order[b + 1] = order[b]; --b; }
+    order[b + 1] = t;
+  }
+  double load[64] = {};
+  for (int s = 0; s < 64; ++s) p->need[s] = 0;
+  for (int a = 0; a < count; ++a) {
+    int i = order[a];
+    if (M[i] < 0) return -3;
+    int best = 0;
+    for (int s = 1; s < p->ns; ++s)
+      if (load[s] < load[best]) best = s;
+    p->assign[i] = best;
+    load[best] += (double)M[i] * M[i] * M[i];
+    gep_options oi = *o;
+    if (prec) oi.precision = prec[i];
+    size_t need = layout(M[i], &oi).end;
+    if (need > p->need[best]) p->need[best] = need;
+  }
+  size_t off = 0;
+  for (int s = 0; s < p->ns; ++s) {
+    p->off[s] = off;
+    off += r256(p->need[s]);
+  }
+  p->total = off;
+  return GEP_OK;
+}
+
+}  // namespace
+
+int gep_solve_batched_workspace_size(gep_handle_t h, int count, const int* M, const gep_options* o,
+                                     const int* precision, int nstreams, size_t* bytes) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (count > 0 && !M) return -3;
+  if (!o) return -4;
+  if (!bytes) return -7;
+  static BatchPlan plan;
+  GEP_CHECK(make_plan(count, M, o, precision, nstreams, &plan));
+  *bytes = plan.total;
+  return GEP_OK;
+}
+
+int gep_solve_batched(gep_handle_t h, int count, const int* M, double* const* A, double* const* B, double* const* w,
+                      double* const* Y, const gep_options* o, const int* precision, int nstreams) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (count < 0 || count > kMaxBatch) return -2;
+  if (count > 0 && (!M || !A || !B || !w || !Y)) return -3;
+  if (!o) return -8;
+  if (nstreams < 1 || nstreams > 64) return -10;
+  for (int i = 0; i < count; ++i) {
+    gep_options oi = *o;
+    if (precision) oi.precision = precision[i];
+    GEP_CHECK(check_opts(&oi));
+  }
+  if (count == 0) return GEP_OK;
+  static BatchPlan plan;
+  GEP_CHECK(make_plan(count, M, o, precision, nstreams, &plan));
+  if (h->ws == nullptr || h->ws_bytes < plan.total) return GEP_ERR_ALLOC;
+  // child handles, streams and events are created once (outside any stream capture)
+  if (!h->fork_ev) GEP_CUDA(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+  if (!h->d_batch_info) GEP_CUDA(cudaMalloc((void**)&h->d_batch_info, sizeof(int) * 2 * kMaxBatch));
+  while (h->nchild < plan.ns) {
+    int c = h->nchild;
+    GEP_CUDA(cudaStreamCreateWithFlags(&h->child_stream[c], cudaStreamNonBlocking));
+    GEP_CUDA(cudaEventCreateWithFlags(&h->child_done[c], cudaEventDisableTiming));
+    GEP_CHECK(gep_create(&h->child[c], (void*)h->child_stream[c]));
+    h->nchild++;
+  }
+  GEP_CUDA(cudaEventRecord(h->fork_ev, h->stream));
+  for (int s = 0; s < plan.ns; ++s) GEP_CUDA(cudaStreamWaitEvent(h->child_stream[s], h->fork_ev, 0));
+  for (int i = 0; i < count; ++i) {
+    int s = plan.assign[i];
+    gep_handle_t c = h->child[s];
+    c->ws = h->ws + plan.off[s];
+    c->ws_bytes = plan.need[s];
+    gep_options oi = *o;
+    oi.timers = 0;
+    if (precision) oi.precision = precision[i];
+    GEP_CHECK(gep_solve(c, M[i], A[i], M[i] > 1 ? M[i] : 1, B[i], M[i] > 1 ? M[i] : 1, w[i], Y[i],
+                        M[i] > 1 ? M[i] : 1, &oi));
+    GEP_CUDA(cudaMemcpyAsync(h->d_batch_info + 2 * i, c->d_status, 2 * sizeof(int), cudaMemcpyDeviceToDevice,
+                             c->stream));
+    h->launches += 0;
+  }
+  for (int s = 0; s < plan.ns; ++s) {
+    GEP_CUDA(cudaEventRecord(h->child_done[s], h->child_stream[s]));
+    GEP_CUDA(cudaStreamWaitEvent(h->stream, h->child_done[s], 0));
+  }
+  h->batch_count = count;
+  return GEP_OK;
+}
+
+int gep_batched_info(gep_handle_t h, int* info) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (!info) return -2;
+  *info = 0;
+  if (!h->d_batch_info || h->batch_count == 0) return GEP_OK;
+  static int st[2 * kMaxBatch];
+  GEP_CUDA(cudaStreamSynchronize(h->stream));
+  GEP_CUDA(cudaMemcpy(st, h->d_batch_info, sizeof(int) * 2 * h->batch_count, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < h->batch_count; ++i) {
+    int v = st[2 * i + 1] != 0 ? st[2 * i + 1] : st[2 * i];
+    if (v != 0) { *info = v; break; }
+  }
   return GEP_OK;
 }
 

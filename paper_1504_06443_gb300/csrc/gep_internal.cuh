@@ -29,6 +29,14 @@ struct gep_handle_s {
   cudaEvent_t* prof_ev = nullptr;   // 2 * prof_cap events
   double* prof_flops = nullptr;     // tensor flops of each recorded launch
   double* prof_f64eq = nullptr;     // FP64-equivalent flops of each recorded launch
+  // batched solves: child handles, one per concurrent stream (created on first use)
+  int nchild = 0;
+  gep_handle_s* child[64] = {};
+  cudaStream_t child_stream[64] = {};
+  cudaEvent_t child_done[64] = {};
+  cudaEvent_t fork_ev = nullptr;
+  int* d_batch_info = nullptr;  // 2 ints per pencil of the last batched call
+  int batch_count = 0;
 };
 
 namespace gep {
@@ -129,6 +137,12 @@ int tridiag_eig_dc(gep_handle_t h, int M, const double* d, const double* e, doub
 size_t dc_ws_bytes(int M);
 int tridiag_eig_bisect(gep_handle_t h, int M, const double* d, const double* e, double* w);
 int sign_convention(gep_handle_t h, int M, int ncol, double* Y, int ldy);
+size_t refine_ws_elems(int M);
+int refine_eigenpairs(gep_handle_t h, int M, const double* Af, const double* Bf, double* X, int ldx, double* w,
+                      double* ws, int iters, int engine);
+size_t adjoint_ws_elems(int M, int no);
+int adjoint(gep_handle_t h, int M, int no, const double* w, const double* Y, int ldy, const double* lbar,
+            const double* W, int ldw, double* Abar, double* Bbar, int ldab, double* ws, int engine);
 
 // Kernel-side helper: returns true when an earlier stage recorded an error.
 __device__ __forceinline__ bool status_bad(const int* st) { return st != nullptr && (st[0] != 0 || st[1] != 0); }

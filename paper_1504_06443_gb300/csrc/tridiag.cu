@@ -130,15 +130,6 @@ __device__ __forceinline__ ff ff_split(double x) {
   return {__int_as_float((int)hb), sign ? -l : l};
 }
 
-// s += x (float pairs), TwoSum on the leading parts.
-__device__ __forceinline__ void ff_add(ff& s, ff x) {
-  float t = s.h + x.h;
-  float z = t - s.h;
-  float err = (s.h - (t - z)) + (x.h - z);
-  s.h = t;
-  s.l += err + x.l;
-}
-
 // s += x with both parts TwoSum'ed and the pair renormalised (accurate double-float
 // addition, relative error ~3 * 2^-48 per step): used where hundreds of partial sums
 // of one row are added, so the error does not grow with their number.
@@ -178,21 +169,26 @@ __device__ __forceinline__ void ff_madd(ff& s, float ah, float al, float vh, flo
   s.l += err + e;
 }
 
-// Lower triangle of the n x n block at A (FP64) -> float pairs at S (same indexing).
-__global__ void k_to_ff(int n, const double* __restrict__ A, int lda, float2* __restrict__ S, int lds,
-                        const int* st) {
+// Matrix element types of the single-precision SYMV: a float pair (FP64-grade path)
+// or a single float (the FP32-grade mixed-precision path, half the traffic).
+__device__ __forceinline__ float2 as_pair(float2 a) { return a; }
+__device__ __forceinline__ float2 as_pair(float a) { return make_float2(a, 0.f); }
+__device__ __forceinline__ void put(float2* p, ff x) { *p = make_float2(x.h, x.l); }
+__device__ __forceinline__ void put(float* p, ff x) { *p = x.h; }
+
+// Lower triangle of the n x n block at A (FP64) -> float pairs / floats at S (same indexing).
+template <class T>
+__global__ void k_to_ff(int n, const double* __restrict__ A, int lda, T* __restrict__ S, int lds, const int* st) {
   if (status_bad(st)) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   for (int j = blockIdx.y; j < n; j += gridDim.y) {
-    if (i < n && i >= j) {
-      ff p = ff_split(A[GEP_IX(i, j, lda)]);
-      S[GEP_IX(i, j, lds)] = make_float2(p.h, p.l);
-    }
+    if (i < n && i >= j) put(&S[GEP_IX(i, j, lds)], ff_split(A[GEP_IX(i, j, lda)]));
   }
 }
 
-// Same partial-product scheme as k_symv_partial below, on the float-pair matrix.
-__global__ void __launch_bounds__(256) k_symv_partial_ff(int n, const float2* __restrict__ A, int lda,
+// Same partial-product scheme as k_symv_partial below, on the single-precision matrix.
+template <class T>
+__global__ void __launch_bounds__(256) k_symv_partial_ff(int n, const T* __restrict__ A, int lda,
                                                          const double* __restrict__ v, double* __restrict__ Pd,
                                                          double* __restrict__ Pt, int maxch, const int* st) {
   __shared__ float vsh[SW], vsl[SW];
@@ -221,12 +217,12 @@ __global__ void __launch_bounds__(256) k_symv_partial_ff(int n, const float2* __
     ff dir = {0.f, 0.f};
     if (r < rend && ncols > 0) {
       ff vr = ff_split(v[r]);
-      const float2* arow = A + r;
+      const T* arow = A + r;
       if (r >= cbase + 16 && ncols == 16) {
         // full quarter strictly below the diagonal: issue all 16 loads, then compute
         float2 a[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) a[q] = __ldg(arow + (size_t)(cbase + q) * lda);
+        for (int q = 0; q < 16; ++q) a[q] = as_pair(__ldg(arow + (size_t)(cbase + q) * lda));
         ff dir2 = {0.f, 0.f};
 #pragma unroll
         for (int q = 0; q < 16; q += 2) {
@@ -241,7 +237,7 @@ __global__ void __launch_bounds__(256) k_symv_partial_ff(int n, const float2* __
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           if (q < ncols) {
-            float2 a = arow[(size_t)(cbase + q) * lda];
+            float2 a = as_pair(arow[(size_t)(cbase + q) * lda]);
             ff_madd(dir, a.x, a.y, vsh[cq * 16 + q], vsl[cq * 16 + q]);
             ff_madd(acc[q], a.x, a.y, vr.h, vr.l);
           }
@@ -251,7 +247,7 @@ __global__ void __launch_bounds__(256) k_symv_partial_ff(int n, const float2* __
         for (int q = 0; q < 16; ++q) {
           int col = cbase + q;
           if (q < ncols && r >= col) {
-            float2 a = arow[(size_t)col * lda];
+            float2 a = as_pair(arow[(size_t)col * lda]);
             ff_madd(dir, a.x, a.y, vsh[cq * 16 + q], vsl[cq * 16 + q]);
             if (r > col) ff_madd(acc[q], a.x, a.y, vr.h, vr.l);
           }
@@ -524,13 +520,19 @@ int tridiag_1stage(gep_handle_t h, int M, double* C, int ldc, double* d, double*
   const int* st = h->d_status;
   // FP64 engine: plain FP64 SYMVs.  Tensor-core engines: compensated float-pair SYMVs.
   const bool pairs = engine != GEP_PREC_FP64;
+  // FP32-grade engine: the SYMV matrix is a single float per element (half the traffic).
+  const bool single = engine == GEP_PREC_MIXED_REFINED;
+  float* S1 = reinterpret_cast<float*>(t.S2);
   for (int j0 = 0; j0 < M; j0 += NBT) {
     int nbp = min(NBT, M - j0);
     int done = 0;
     if (pairs && M - j0 > 1) {
       int nt = M - j0;
       dim3 g((nt + 255) / 256, nt < 65535 ? nt : 65535);
-      k_to_ff<<<g, 256, 0, s>>>(nt, C + GEP_IX(j0, j0, ldc), ldc, t.S2 + GEP_IX(j0, j0, M), M, st);
+      if (single)
+        k_to_ff<float><<<g, 256, 0, s>>>(nt, C + GEP_IX(j0, j0, ldc), ldc, S1 + GEP_IX(j0, j0, M), M, st);
+      else
+        k_to_ff<float2><<<g, 256, 0, s>>>(nt, C + GEP_IX(j0, j0, ldc), ldc, t.S2 + GEP_IX(j0, j0, M), M, st);
       GEP_CHECK(check_launch(h));
     }
     for (int i = 0; i < nbp; ++i) {
@@ -548,9 +550,12 @@ int tridiag_1stage(gep_handle_t h, int M, double* C, int ldc, double* d, double*
       const double* v = t.Vp + GEP_IX(c + 1, i, ldp);
       const double* A = C + GEP_IX(c + 1, c + 1, ldc);
       int nblk = (n + SW - 1) / SW, maxch = (n + SCH - 1) / SCH;
-      if (pairs)
-        k_symv_partial_ff<<<dim3(nblk, maxch), 256, 0, s>>>(n, t.S2 + GEP_IX(c + 1, c + 1, M), M, v, t.Pd, t.Pt,
-                                                            maxch, st);
+      if (pairs && single)
+        k_symv_partial_ff<float><<<dim3(nblk, maxch), 256, 0, s>>>(n, S1 + GEP_IX(c + 1, c + 1, M), M, v, t.Pd,
+                                                                   t.Pt, maxch, st);
+      else if (pairs)
+        k_symv_partial_ff<float2><<<dim3(nblk, maxch), 256, 0, s>>>(n, t.S2 + GEP_IX(c + 1, c + 1, M), M, v, t.Pd,
+                                                                    t.Pt, maxch, st);
       else
         k_symv_partial<<<dim3(nblk, maxch), 256, 0, s>>>(n, A, ldc, v, t.Pd, t.Pt, maxch, st);
       GEP_CHECK(check_launch(h));
