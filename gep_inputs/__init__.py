@@ -59,6 +59,33 @@ def known_spectrum(M: int, seed: int):
     return dict(A=np.ascontiguousarray(A), B=np.ascontiguousarray(B), lam=lam, L0=L0, Q=Q)
 
 
+def clustered_spectrum(M: int, seed: int):
+    """known_spectrum's construction with tight clusters planted in the spectrum: groups
+    of 2..6 eigenvalues spaced 1e-9 apart and groups of exactly repeated eigenvalues
+    (the case first-order eigenpair corrections cannot take).  Returns dict(A, B, lam)."""
+    rng = np.random.default_rng(seed)
+    L0 = np.tril(rng.normal(0.0, 0.05, size=(M, M)), -1)
+    L0[np.diag_indices(M)] = rng.uniform(1.0, 2.0, size=M)
+    G = rng.standard_normal((M, M))
+    Q, R = np.linalg.qr(G)
+    Q = Q * np.where(np.diag(R) < 0, -1.0, 1.0)[None, :]
+    lam = rng.uniform(-20.0, 20.0, size=M)
+    i = 0
+    while i + 6 < M:
+        k = int(rng.integers(2, 7))
+        if rng.random() < 0.5:
+            lam[i:i + k] = lam[i] + 1e-9 * np.arange(k)
+        else:
+            lam[i:i + k] = lam[i]
+        i += k + int(rng.integers(5, 40))
+    X = L0 @ Q
+    A = (X * lam[None, :]) @ X.T
+    A = 0.5 * (A + A.T)
+    B = L0 @ L0.T
+    B = 0.5 * (B + B.T)
+    return dict(A=np.ascontiguousarray(A), B=np.ascontiguousarray(B), lam=lam)
+
+
 def _box(n_atoms: int) -> float:
     return (n_atoms / DENSITY) ** (1.0 / 3.0)
 

@@ -69,7 +69,7 @@ typedef struct gep_options {
   int want_vectors; /* 1: eigenpairs (T_full); 0: eigenvalues only (T_evo)        */
   int overwrite;    /* 1: A and B may be destroyed by gep_solve (saves two copies) */
   int timers;       /* 1: record per-stage CUDA-event times (gep_get_stage_times) */
-  int refine_iters; /* GEP_PREC_MIXED_REFINED: FP64 refinement steps (0 = default, 2)  */
+  int refine_iters; /* GEP_PREC_MIXED_REFINED: FP64 refinement steps; 0 = until converged */
 } gep_options;
 
 /* Fills *o with the defaults: TWOSIDED, 1STAGE, b = 0, FP64, vectors, no overwrite, no timers.
@@ -77,7 +77,10 @@ typedef struct gep_options {
  * on the FP32-grade split-BF16 engine and the SYMVs in FP32; FP64 stays in the diagonal
  * blocks, the secular equations and deflation; then all eigenpairs are refined in FP64
  * (B-Rayleigh quotients and the first-order correction X <- X (I + E) from S = X^T A X,
- * R = X^T B X formed with FP64-accurate products). */
+ * R = X^T B X formed with FP64-accurate products; pairs whose gap is below
+ * max(64 |S_ij - lambda_j R_ij|, 16 max_ij |S_ij - lambda_j R_ij|, 1e-6 max|lambda|) are
+ * grouped into clusters of up to 32 eigenpairs whose k x k pencil (S_CC, R_CC) is solved
+ * exactly). */
 void gep_default_options(gep_options* o);
 
 /* Creates a handle bound to `stream` (a cudaStream_t passed as void*; NULL = legacy
@@ -184,6 +187,15 @@ int gep_reset_info(gep_handle_t h);
  * t[5] back-substitution (R5 / Eq. 6), t[6] FP64 refinement (mixed precision only, else ~0).
  * Synchronises. */
 int gep_get_stage_times(gep_handle_t h, double t[7]);
+
+/* FP64 refinement steps the last GEP_PREC_MIXED_REFINED gep_solve on h took (or
+ * GEP_ERR_HANDLE).  With refine_iters = 0 the refinement stops after the step whose
+ * size (largest first-order correction |E_ij|, B-orthogonality defect inside clusters,
+ * |1 - y_i^T B y_i|) is at most 1e-8, and after 8 steps at most; that test synchronises
+ * the stream once per step, so while h's stream is being captured into a CUDA graph a
+ * fixed 4 steps run instead.  (No counterpart in the paper: the refinement is this
+ * library's mixed-precision extension.) */
+int gep_refine_steps(gep_handle_t h);
 
 /* Number of kernels the library launched since gep_create / last reset. */
 long long gep_launch_count(gep_handle_t h, int reset);

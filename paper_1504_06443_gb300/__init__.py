@@ -89,6 +89,7 @@ def load():
             "gep_reset_info": (_I, [_P]),
             "gep_get_stage_times": (_I, [_P, ctypes.POINTER(_D)]),
             "gep_launch_count": (ctypes.c_longlong, [_P, _I]),
+            "gep_refine_steps": (_I, [_P]),
             "gep_profile_enable": (_I, [_P, _I]),
             "gep_profile_read": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D),
                                       ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), _I]),
@@ -197,6 +198,10 @@ class Handle:
     def launches(self, reset=False):
         return int(self.lib.gep_launch_count(self.h, 1 if reset else 0))
 
+    def refine_steps(self):
+        """FP64 refinement steps the last mixed-precision solve on this handle took."""
+        return int(self.lib.gep_refine_steps(self.h))
+
     def profile_enable(self, cap):
         _check(self.lib.gep_profile_enable(self.h, int(cap)), "gep_profile_enable")
 
@@ -222,7 +227,7 @@ def default_handle():
 
 
 def make_options(reducer="twosided", sep="1stage", precision="fp64", want_vectors=True, overwrite=False,
-                 timers=False, bandwidth=0):
+                 timers=False, bandwidth=0, refine_iters=0):
     o = GepOptions()
     load().gep_default_options(ctypes.byref(o))
     o.reducer = _REDUCERS[reducer] if isinstance(reducer, str) else int(reducer)
@@ -232,6 +237,7 @@ def make_options(reducer="twosided", sep="1stage", precision="fp64", want_vector
     o.overwrite = 1 if overwrite else 0
     o.timers = 1 if timers else 0
     o.bandwidth = int(bandwidth)
+    o.refine_iters = int(refine_iters)
     return o
 
 
@@ -244,7 +250,7 @@ def workspace_bytes(M, handle=None, **opts):
 
 
 def solve(A, B, reducer="twosided", sep="1stage", precision="fp64", want_vectors=True, overwrite=False,
-          timers=False, bandwidth=0, handle=None, out=None):
+          timers=False, bandwidth=0, handle=None, out=None, refine_iters=0):
     """All eigenpairs of A y = lambda B y (A, B symmetric float64 CUDA tensors, B SPD).
 
     Returns (w, Y, info): w ascending, Y (column-major view) B-orthonormal or None.
@@ -252,7 +258,7 @@ def solve(A, B, reducer="twosided", sep="1stage", precision="fp64", want_vectors
     torch = _torch()
     h = handle or default_handle()
     M = int(A.shape[0])
-    o = make_options(reducer, sep, precision, want_vectors, overwrite, timers, bandwidth)
+    o = make_options(reducer, sep, precision, want_vectors, overwrite, timers, bandwidth, refine_iters)
     n = _SZ()
     _check(h.lib.gep_workspace_size(h.h, M, ctypes.byref(o), ctypes.byref(n)), "gep_workspace_size")
     h.ensure_workspace(n.value)

@@ -183,6 +183,11 @@ long long gep_launch_count(gep_handle_t h, int reset) {
   return n;
 }
 
+int gep_refine_steps(gep_handle_t h) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  return h->refine_steps;
+}
+
 int gep_profile_enable(gep_handle_t h, int cap) {
   if (!handle_ok(h)) return GEP_ERR_HANDLE;
   if (cap < 0) return -2;
@@ -479,8 +484,7 @@ int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, dou
   }
   mark(h, o, 6);
   if (mixed) {
-    int iters = o->refine_iters > 0 ? o->refine_iters : 2;
-    GEP_CHECK(refine_eigenpairs(h, M, Af, Bf, Y, ldy, w, (double*)uni, iters, GEP_PREC_FP64_EMULATED));
+    GEP_CHECK(refine_eigenpairs(h, M, Af, Bf, Y, ldy, w, (double*)uni, o->refine_iters, GEP_PREC_FP64_EMULATED));
   }
   mark(h, o, 7);
   GEP_CHECK(sign_convention(h, M, M, Y, ldy));

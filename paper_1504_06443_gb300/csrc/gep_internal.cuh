@@ -37,6 +37,7 @@ struct gep_handle_s {
   cudaEvent_t fork_ev = nullptr;
   int* d_batch_info = nullptr;  // 2 ints per pencil of the last batched call
   int batch_count = 0;
+  int refine_steps = 0;  // FP64 refinement steps taken by the last mixed-precision solve
 };
 
 namespace gep {

@@ -46,3 +46,32 @@ def test_mixed_known_spectrum(gep):
     w, Y, info = gep.solve(dev(g["A"]), dev(g["B"]), precision="mixed_refined")
     assert info == 0
     assert np.max(np.abs(w.cpu().numpy() - np.sort(g["lam"]))) <= 1e-11 * 20.0
+
+
+def test_mixed_clustered_spectrum(gep):
+    """Planted clusters (1e-9 spacings and exact repeats) go through the exact cluster
+    solve of the refinement; eigenvalues, residual and B-orthogonality reach FP64 level."""
+    M = 384
+    g = gi.clustered_spectrum(M, seed=11)
+    A, B = g["A"], g["B"]
+    h = gep.Handle()
+    w, Y, info = gep.solve(dev(A), dev(B), precision="mixed_refined", handle=h)
+    assert info == 0
+    steps = h.refine_steps()
+    assert 1 <= steps <= 8
+    wh, Yh = w.cpu().numpy(), Y.cpu().numpy()
+    assert np.max(np.abs(wh - np.sort(g["lam"]))) <= 1e-11 * 20.0
+    res = np.linalg.norm(A @ Yh - (B @ Yh) * wh[None, :]) / (np.linalg.norm(A) * M)
+    orth = np.max(np.abs(Yh.T @ B @ Yh - np.eye(M)))
+    assert res <= 1e-13, res
+    assert orth <= 1e-12, orth
+
+
+def test_mixed_fixed_step_count(gep):
+    """refine_iters > 0 runs exactly that many steps; the adaptive default stops on its own."""
+    tb = gi.tight_binding(260, seed=267)
+    h = gep.Handle()
+    gep.solve(dev(tb["A"]), dev(tb["B"]), precision="mixed_refined", handle=h, refine_iters=3)
+    assert h.refine_steps() == 3
+    gep.solve(dev(tb["A"]), dev(tb["B"]), precision="mixed_refined", handle=h)
+    assert 1 <= h.refine_steps() <= 8
