@@ -64,7 +64,7 @@ typedef struct gep_handle_s* gep_handle_t;
 typedef struct gep_options {
   int reducer;      /* GEP_RED_*                                                  */
   int sep;          /* GEP_SEP_*                                                  */
-  int bandwidth;    /* band width b for GEP_SEP_2STAGE (0 = library default)      */
+  int bandwidth;    /* band width b for GEP_SEP_2STAGE, 1..64 (0 = library default, 64) */
   int precision;    /* GEP_PREC_*                                                 */
   int want_vectors; /* 1: eigenpairs (T_full); 0: eigenvalues only (T_evo)        */
   int overwrite;    /* 1: A and B may be destroyed by gep_solve (saves two copies) */
@@ -125,6 +125,28 @@ int sep_tridiag_eig(gep_handle_t h, int M, const double* d, const double* e, dou
                     int ldz, int want_vectors);
 int sep_backtransform(gep_handle_t h, int M, int ncol, const double* C, int ldc, const double* tau,
                       double* Z, int ldz);
+
+/* ---- two-stage SEP solver (section 3: the narrow-band reduction solvers ELPA2 and
+ * Eigen_sx; "TRD/BAND" and "BACK" of Table 3) --------------------------------------
+ * sep_q2_elems: number of doubles of the bulge-chasing reflector storage q2 for order M
+ *   and bandwidth b (1 <= b <= 64; 0 for invalid arguments).
+ * sep_tridiag_2stage: C = Q1 Q2 T Q2^T Q1^T in two stages.  Full -> band: C (lower on
+ *   entry; both triangles are overwritten) becomes a matrix of bandwidth b, whose
+ *   lower band (offsets 0..b) is kept, with the panel reflectors stored below the band
+ *   (reflector j has its implied unit entry at row j+b) and their scalars in tau1[M]
+ *   (tau1[j] = 0 where no reflector exists).  Band -> tridiagonal by bulge chasing:
+ *   d[M], e[M-1] receive T; q2 (device, sep_q2_elems(M, b) doubles, caller-owned;
+ *   NULL when only eigenvalues are wanted) receives the bulge-chasing reflectors.
+ *   C's band itself is not modified by the second stage.
+ * sep_backtransform_2stage: Z (M x ncol) is overwritten by Q1 (Q2 Z) using C, tau1 and
+ *   q2 from sep_tridiag_2stage with the same M and b.
+ * Both take their scratch from the handle workspace (size it with gep_workspace_size
+ * and sep = GEP_SEP_2STAGE, bandwidth = b); products run in FP64. */
+size_t sep_q2_elems(int M, int b);
+int sep_tridiag_2stage(gep_handle_t h, int M, double* C, int ldc, int b, double* d, double* e, double* tau1,
+                       double* q2);
+int sep_backtransform_2stage(gep_handle_t h, int M, int ncol, int b, const double* C, int ldc,
+                             const double* tau1, const double* q2, double* Z, int ldz);
 
 /* ---- whole workflow ------------------------------------------------------------
  * gep_solve: Eq. 2 for all M eigenpairs.  A, B (lower) are read and preserved unless

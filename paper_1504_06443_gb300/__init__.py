@@ -18,7 +18,7 @@ import os
 import threading
 
 __all__ = ["load", "solve", "solve_host", "cholesky", "reduce", "tridiag_1stage", "tridiag_eig",
-           "sep_backtransform", "gep_backtransform", "dgemm", "Handle", "default_handle",
+           "sep_backtransform", "tridiag_2stage", "sep_backtransform_2stage", "gep_backtransform", "dgemm", "Handle", "default_handle",
            "RED_TWOSIDED", "RED_EXPLICIT_INV", "SEP_1STAGE", "SEP_2STAGE", "PREC_FP64",
            "PREC_FP64_EMULATED", "PREC_MIXED_REFINED", "GepError"]
 
@@ -83,6 +83,9 @@ def load():
             "sep_tridiag_1stage": (_I, [_P, _I, _P, _I, _P, _P, _P]),
             "sep_tridiag_eig": (_I, [_P, _I, _P, _P, _P, _P, _I, _I]),
             "sep_backtransform": (_I, [_P, _I, _I, _P, _I, _P, _P, _I]),
+            "sep_q2_elems": (_SZ, [_I, _I]),
+            "sep_tridiag_2stage": (_I, [_P, _I, _P, _I, _I, _P, _P, _P, _P]),
+            "sep_backtransform_2stage": (_I, [_P, _I, _I, _I, _P, _I, _P, _P, _P, _I]),
             "gep_solve": (_I, [_P, _I, _P, _I, _P, _I, _P, _P, _I, ctypes.POINTER(GepOptions)]),
             "gep_solve_host": (_I, [_P, _I, _P, _I, _P, _I, _P, _P, _I, ctypes.POINTER(GepOptions)]),
             "gep_get_info": (_I, [_P, ctypes.POINTER(_I)]),
@@ -387,6 +390,43 @@ def sep_backtransform(C_refl, tau, Z, handle=None):
         tt[: M - 1] = tau[: M - 1]
     h.ensure_workspace(_stage_ws(M, ncol))
     _check(h.lib.sep_backtransform(h.h, M, ncol, _ptr(Cc), _ld(Cc), _ptr(tt), _ptr(Y), _ld(Y)), "sep_backtransform")
+    return Y
+
+
+def _two_stage_ws(h, M, b):
+    o = make_options(sep="2stage", bandwidth=b)
+    n = _SZ()
+    _check(h.lib.gep_workspace_size(h.h, M, ctypes.byref(o), ctypes.byref(n)), "gep_workspace_size")
+    return n.value
+
+
+def tridiag_2stage(C, b=64, want_q2=True, handle=None):
+    """Two-stage reduction (full -> band of width b -> tridiagonal):
+    (d, e, tau1, q2 or None, C with the band and the panel reflectors)."""
+    torch = _torch()
+    h = handle or default_handle()
+    Cc = colmajor(C.clone())
+    M = Cc.shape[0]
+    d = torch.empty(max(M, 1), dtype=torch.float64, device=C.device)
+    e = torch.zeros(max(M, 1), dtype=torch.float64, device=C.device)
+    tau1 = torch.zeros(max(M, 1), dtype=torch.float64, device=C.device)
+    nq = int(h.lib.sep_q2_elems(M, int(b)))
+    q2 = torch.empty(max(nq, 1), dtype=torch.float64, device=C.device) if want_q2 else None
+    h.ensure_workspace(_two_stage_ws(h, M, b))
+    _check(h.lib.sep_tridiag_2stage(h.h, M, _ptr(Cc), _ld(Cc), int(b), _ptr(d), _ptr(e), _ptr(tau1), _ptr(q2)),
+           "sep_tridiag_2stage")
+    return d[:M], e[: max(M - 1, 0)], tau1[:M], q2, Cc
+
+
+def sep_backtransform_2stage(C_refl, tau1, q2, b, Z, handle=None):
+    """Z <- Q1 (Q2 Z) with the output of tridiag_2stage."""
+    h = handle or default_handle()
+    Y = colmajor(Z.clone())
+    Cc = colmajor(C_refl)
+    M, ncol = Y.shape
+    h.ensure_workspace(max(_two_stage_ws(h, M, b), _stage_ws(M, ncol)))
+    _check(h.lib.sep_backtransform_2stage(h.h, M, ncol, int(b), _ptr(Cc), _ld(Cc), _ptr(tau1.contiguous()),
+                                          _ptr(q2), _ptr(Y), _ld(Y)), "sep_backtransform_2stage")
     return Y
 
 

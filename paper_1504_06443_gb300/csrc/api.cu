@@ -15,9 +15,14 @@ constexpr int NB = 128;  // diagonal block order of the triangular kernels (tri.
 bool handle_ok(gep_handle_t h) { return h != nullptr && h->magic == 0x6e70; }
 
 struct SolveLayout {
-  size_t Cw, Lw, invD, vec, uni, eng, af, end;  // byte offsets
+  size_t Cw, Lw, invD, vec, uni, eng, af, q2, end;  // byte offsets
   size_t uni_bytes, eng_bytes;
 };
+
+constexpr int kDefaultBand = 64;  // bandwidth of the two-stage reduction when o->bandwidth = 0
+
+int band_of(const gep_options* o) { return o->bandwidth > 0 ? o->bandwidth : kDefaultBand; }
+bool two_stage(const gep_options* o) { return o->sep == GEP_SEP_2STAGE; }
 
 size_t r256(size_t x) { return align256(x); }
 
@@ -30,7 +35,7 @@ size_t union_bytes(int M, const gep_options* o) {
   size_t mm = (size_t)M * M * sizeof(double);
   size_t tmpb = (size_t)NB * M * sizeof(double);
   size_t red = (o->reducer == GEP_RED_EXPLICIT_INV) ? r256(mm) + r256(mm) + r256(tmpb) : r256(mm) + r256(tmpb);
-  size_t tri = tridiag_ws_elems(M) * sizeof(double);
+  size_t tri = two_stage(o) ? band_ws_elems(M, band_of(o)) * sizeof(double) : tridiag_ws_elems(M) * sizeof(double);
   size_t dc = o->want_vectors ? dc_ws_bytes(M) : 0;
   size_t bt = o->want_vectors ? backtransform_ws_elems(M, M) * sizeof(double) : 0;
   size_t r3 = o->want_vectors ? (r256(tmpb) + (o->reducer == GEP_RED_EXPLICIT_INV ? r256(mm) : 0)) : 0;
@@ -60,6 +65,8 @@ SolveLayout layout(int M, const gep_options* o) {
   off += L.eng_bytes;
   L.af = off;  // full symmetric A and B kept for the FP64 refinement
   off += (o->precision == GEP_PREC_MIXED_REFINED) ? 2 * r256(mm) : 0;
+  L.q2 = off;  // bulge-chasing reflectors, kept from S1c to the back-transformation
+  off += (two_stage(o) && o->want_vectors) ? r256(q2_elems(M, band_of(o)) * sizeof(double)) : 0;
   L.end = off;
   return L;
 }
@@ -67,7 +74,8 @@ SolveLayout layout(int M, const gep_options* o) {
 int check_opts(const gep_options* o) {
   if (!o) return -1;
   if (o->reducer != GEP_RED_TWOSIDED && o->reducer != GEP_RED_EXPLICIT_INV) return GEP_ERR_UNSUPPORTED;
-  if (o->sep != GEP_SEP_1STAGE) return GEP_ERR_UNSUPPORTED;
+  if (o->sep != GEP_SEP_1STAGE && o->sep != GEP_SEP_2STAGE) return GEP_ERR_UNSUPPORTED;
+  if (o->sep == GEP_SEP_2STAGE && (o->bandwidth < 0 || o->bandwidth > 64)) return GEP_ERR_UNSUPPORTED;
   if (o->precision != GEP_PREC_FP64 && o->precision != GEP_PREC_FP64_EMULATED &&
       o->precision != GEP_PREC_MIXED_REFINED)
     return GEP_ERR_UNSUPPORTED;
@@ -399,6 +407,51 @@ int sep_backtransform(gep_handle_t h, int M, int ncol, const double* C, int ldc,
   return backtransform_q(h, M, ncol, C, ldc, tau, Z, ldz, ws, n, GEP_PREC_FP64);
 }
 
+size_t sep_q2_elems(int M, int b) {
+  if (M < 0 || b < 1 || b > 64) return 0;
+  return q2_elems(M, b);
+}
+
+int sep_tridiag_2stage(gep_handle_t h, int M, double* C, int ldc, int b, double* d, double* e, double* tau1,
+                       double* q2) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (M < 0) return -2;
+  if (M > 0 && !C) return -3;
+  if (ldc < (M > 1 ? M : 1)) return -4;
+  if (b < 1 || b > 64) return -5;
+  if (M > 0 && !d) return -6;
+  if (M > 1 && !e) return -7;
+  if (M > 0 && !tau1) return -8;
+  if (M == 0) return GEP_OK;
+  Arena ar(h->ws, h->ws_bytes);
+  size_t n = band_ws_elems(M, b);
+  double* ws = ar.take<double>(n);
+  if (!ar.ok) return GEP_ERR_ALLOC;
+  GEP_CHECK(band_reduce(h, M, C, ldc, b, tau1, ws, n, GEP_PREC_FP64));
+  return band_to_tridiag(h, M, C, ldc, b, d, e, q2, ws, n);
+}
+
+int sep_backtransform_2stage(gep_handle_t h, int M, int ncol, int b, const double* C, int ldc, const double* tau1,
+                             const double* q2, double* Z, int ldz) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (M < 0) return -2;
+  if (ncol < 0) return -3;
+  if (b < 1 || b > 64) return -4;
+  if (M > 0 && !C) return -5;
+  if (ldc < (M > 1 ? M : 1)) return -6;
+  if (M > 0 && !tau1) return -7;
+  if (M > 2 && !q2) return -8;
+  if (M > 0 && ncol > 0 && !Z) return -9;
+  if (ldz < (M > 1 ? M : 1)) return -10;
+  if (M <= 1 || ncol == 0) return GEP_OK;
+  Arena ar(h->ws, h->ws_bytes);
+  size_t n = backtransform_ws_elems(M, ncol);
+  double* ws = ar.take<double>(n);
+  if (!ar.ok) return GEP_ERR_ALLOC;
+  GEP_CHECK(apply_q2(h, M, b, q2, Z, ldz, ncol));
+  return backtransform_q(h, M, ncol, C, ldc, tau1, Z, ldz, ws, n, GEP_PREC_FP64, b);
+}
+
 int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, double* w, double* Y,
               int ldy, const gep_options* o) {
   if (!handle_ok(h)) return GEP_ERR_HANDLE;
@@ -460,7 +513,15 @@ int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, dou
     }
   }
   mark(h, o, 2);
-  GEP_CHECK(tridiag_1stage(h, M, Cw, ldcw, dvec, evec, tvec, (double*)uni, Ly.uni_bytes / sizeof(double), eng));
+  const int bw = band_of(o);
+  double* q2 = (two_stage(o) && o->want_vectors) ? (double*)(base + Ly.q2) : nullptr;
+  if (two_stage(o)) {
+    GEP_CHECK(band_reduce(h, M, Cw, ldcw, bw, tvec, (double*)uni, Ly.uni_bytes / sizeof(double), eng));   // S1b
+    GEP_CHECK(band_to_tridiag(h, M, Cw, ldcw, bw, dvec, evec, q2, (double*)uni,
+                              Ly.uni_bytes / sizeof(double)));  // S1c
+  } else {
+    GEP_CHECK(tridiag_1stage(h, M, Cw, ldcw, dvec, evec, tvec, (double*)uni, Ly.uni_bytes / sizeof(double), eng));
+  }
   mark(h, o, 3);
   if (!o->want_vectors) {
     GEP_CHECK(tridiag_eig_bisect(h, M, dvec, evec, w));
@@ -473,7 +534,13 @@ int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, dou
   }
   GEP_CHECK(tridiag_eig_dc(h, M, dvec, evec, w, Y, ldy, (double*)uni, Ly.uni_bytes, eng));  // D&C
   mark(h, o, 4);
-  GEP_CHECK(backtransform_q(h, M, M, Cw, ldcw, tvec, Y, ldy, (double*)uni, Ly.uni_bytes / sizeof(double), eng));
+  if (two_stage(o)) {
+    GEP_CHECK(apply_q2(h, M, bw, q2, Y, ldy, M));
+    GEP_CHECK(backtransform_q(h, M, M, Cw, ldcw, tvec, Y, ldy, (double*)uni, Ly.uni_bytes / sizeof(double), eng,
+                              bw));
+  } else {
+    GEP_CHECK(backtransform_q(h, M, M, Cw, ldcw, tvec, Y, ldy, (double*)uni, Ly.uni_bytes / sizeof(double), eng));
+  }
   mark(h, o, 5);
   if (o->reducer == GEP_RED_TWOSIDED) {
     GEP_CHECK(trsm_llt(h, M, M, Lw, ldlw, invD, NB, Y, ldy, (double*)uni, eng));  // Eq. 6

@@ -1,0 +1,553 @@
+// SEP solver, two-stage path: the narrow-band reduction SEP solvers of section 3
+// (ELPA2 / Eigen_sx), stages "TRD/BAND" and "BACK" of Table 3.
+//
+// S1b full -> band.  C = Q1 C_b Q1^T with C_b of bandwidth b.  For each panel of b
+// columns the n x b block below the band is QR-factorised with Householder
+// reflectors (Q_p = I - V T V^T), R stays in the band and the trailing matrix takes
+// the two-sided update
+//     X = C22 V T,  W = X - V (T^T V^T X) / 2,  C22 <- C22 - W V^T - V W^T,
+// i.e. all O(M^3) work is matrix products (split-BF16 tensor-core engine).  C is kept
+// fully symmetric during this stage so that C22 V is a plain product.
+//
+// S1c band -> tridiagonal (bulge chasing).  Sweep s annihilates column s below the
+// subdiagonal with a reflector H(s,0) on rows s+1..s+b, then chases the bulge that
+// the right-application creates one b x b block further down per step:
+//     step k: B = C(st_k:, st_{k-1}:) <- B H(s,k-1);  H(s,k) annihilates B(1:, 0);
+//             B <- H(s,k) B;  D = C(st_k:, st_k:) <- H(s,k) D H(s,k),
+// st_k = s + 1 + k b.  Step k of sweep s+1 only needs step k+1 of sweep s to be done,
+// so sweeps run concurrently on different CTAs, each one step-pipelined behind the
+// previous sweep (progress counters with acquire/release, bounded waits).
+//
+// Back-transformation.  Z = Q1 (Q2 Z_T), Q2 = prod_s prod_k H(s,k).  The reflectors
+// H(s,k) of the b sweeps s0..s0+b-1 of group j (s0 = j b) at the same step k occupy a
+// (2b-1)-row "diamond" G(j,k) = H(s0,k) ... H(s0+b-1,k), and
+//     Q2 = prod_{j ascending} prod_{k descending} G(j,k),
+// because H(s,k) commutes with every H(s',k') (s' < s, k' < k) it has to pass.  The
+// diamonds are applied in wavefronts t = (J - j) + k: diamonds of one wavefront touch
+// disjoint rows and every diamond that must precede one of them lies in an earlier
+// wavefront.  Q1 is applied with the compact-WY back-transformation of the 1-stage
+// path, its reflectors starting b rows (instead of one) below their column.
+#include <math.h>
+
+#include "gep_internal.cuh"
+
+namespace gep {
+namespace {
+
+constexpr int BMAX = 64;      // largest bandwidth
+constexpr int PQ_ROWS = 256;  // panel rows per CTA in the panel QR (one per thread)
+constexpr int PQ_CH = 16;     // columns per reduction chunk in the panel QR
+
+size_t rr(size_t n) { return (n + 31) & ~(size_t)31; }
+
+// ------------------------------------------------------------------ S1b panel QR
+
+// One Householder step (column c) of the QR factorisation of the n x nb panel P (ld ldp),
+// fused with the partial dot products the next step needs.  part_in[g][j] (g over the
+// CTAs) = sum over rows r > c of P(r,c) P(r,j), prow_in[j] = P(c,j): the pivot row is
+// kept out of the sums so that the norm of the tail is never formed by cancellation.
+// c = -1 only produces part/prow for column 0.  The reflector follows LAPACK's dlarfg:
+// beta = -sign(alpha) ||x||, tau = (beta - alpha) / beta, v = [1; x(1:) / (alpha - beta)].
+__global__ void __launch_bounds__(PQ_ROWS) k_pqr_step(int n, int nb, int c, double* __restrict__ P, int ldp,
+                                                      const double* __restrict__ part_in,
+                                                      const double* __restrict__ prow_in,
+                                                      double* __restrict__ part_out, double* __restrict__ prow_out,
+                                                      double* __restrict__ tau, const int* st) {
+  __shared__ double sd[BMAX], sw[BMAX], sc[3];
+  __shared__ double prod[PQ_ROWS][PQ_CH + 1];
+  __shared__ double seg[PQ_ROWS / PQ_CH][PQ_CH];
+  if (status_bad(st)) return;
+  const int t = threadIdx.x, G = gridDim.x;
+  const int r = blockIdx.x * PQ_ROWS + t;
+  double tk = 0.0, scale = 0.0, beta = 0.0;
+  if (c >= 0) {
+    if (t < nb && t >= c) {
+      double s = 0.0;
+      for (int g = 0; g < G; ++g) s += part_in[(size_t)g * BMAX + t];
+      sd[t] = s;
+    }
+    __syncthreads();
+    if (t == 0) {
+      double alpha = prow_in[c], xn2 = sd[c];
+      double tt = 0.0, sl = 0.0, be = alpha;
+      if (xn2 > 0.0) {
+        be = -copysign(sqrt(alpha * alpha + xn2), alpha);
+        tt = (be - alpha) / be;
+        sl = 1.0 / (alpha - be);
+      }
+      sc[0] = tt;
+      sc[1] = sl;
+      sc[2] = be;
+      if (blockIdx.x == 0) tau[c] = tt;
+    }
+    __syncthreads();
+    tk = sc[0];
+    scale = sc[1];
+    beta = sc[2];
+    if (t < nb && t > c) sw[t] = prow_in[t] + scale * sd[t];  // v^T P(:, t)
+    __syncthreads();
+  }
+  const int nc = c + 1;  // pivot column of the next step
+  // this row: reflector entry and the new value of P(r, nc)
+  double vr = 0.0, pn = 0.0;
+  bool live = r < n && r >= (c < 0 ? 0 : c);
+  if (live && c >= 0) {
+    if (r == c) {
+      P[r + (size_t)c * ldp] = beta;
+    } else {
+      vr = P[r + (size_t)c * ldp] * scale;
+      P[r + (size_t)c * ldp] = vr;
+    }
+  }
+  if (live && nc < nb) {
+    double x = (c >= 0 && r == c) ? prow_in[nc] : P[r + (size_t)nc * ldp];
+    if (c >= 0) x -= tk * (r == c ? 1.0 : vr) * sw[nc];
+    pn = x;
+  }
+  for (int cb = (nc < 0 ? 0 : nc); cb < nb; cb += PQ_CH) {
+    for (int q = 0; q < PQ_CH; ++q) {
+      int j = cb + q;
+      double pr = 0.0;
+      if (live && j < nb) {
+        double x = (c >= 0 && r == c) ? prow_in[j] : P[r + (size_t)j * ldp];
+        if (c >= 0) {
+          x -= tk * (r == c ? 1.0 : vr) * sw[j];
+          P[r + (size_t)j * ldp] = x;
+        }
+        if (r == nc) prow_out[j] = x;
+        if (r > nc) pr = pn * x;
+      }
+      prod[t][q] = pr;
+    }
+    __syncthreads();
+    {
+      int q = t % PQ_CH, sg = t / PQ_CH;
+      double s = 0.0;
+      for (int i = 0; i < PQ_CH; ++i) s += prod[sg * PQ_CH + i][q];
+      seg[sg][q] = s;
+    }
+    __syncthreads();
+    if (t < PQ_CH && cb + t < nb) {
+      double s = 0.0;
+      for (int sg = 0; sg < PQ_ROWS / PQ_CH; ++sg) s += seg[sg][t];
+      part_out[(size_t)blockIdx.x * BMAX + cb + t] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// V (n x nb, ld n): unit lower trapezoidal factor of the panel QR stored in P.
+__global__ void k_panel_v(int n, int nb, const double* __restrict__ P, int ldp, double* __restrict__ V,
+                          const int* st) {
+  if (status_bad(st)) return;
+  int r = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y;
+  if (r >= n || q >= nb) return;
+  V[r + (size_t)q * n] = r < q ? 0.0 : (r == q ? 1.0 : P[r + (size_t)q * ldp]);
+}
+
+// ------------------------------------------------------------------ S1c bulge chasing
+
+// Lower band storage with room for the bulge: AB[o + j*ldab] = C(j + o, j), 0 <= o < 2b.
+__global__ void k_band_copy(int M, int b, const double* __restrict__ C, int ldc, double* __restrict__ AB, int ldab,
+                            const int* st) {
+  if (status_bad(st)) return;
+  int o = threadIdx.x, j = blockIdx.x;
+  if (o >= ldab || j >= M) return;
+  AB[o + (size_t)j * ldab] = (o <= b && j + o < M) ? C[(j + o) + (size_t)j * ldc] : 0.0;
+}
+
+__device__ __forceinline__ unsigned long long gclock() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int bulge_steps(int M, int b, int s) { return (M - 2 - s) / b + 1; }
+
+struct BulgeArgs {
+  int M, b, ldab, Q;  // Q = (M - 2) / b: groups 0..Q of b sweeps
+  double* AB;
+  int* prog;          // prog[s] = steps of sweep s completed
+  double* q2;         // diamond storage (or null)
+  int* st;
+};
+
+// Diamond (j, k) base in the reflector storage: [V: 2b x b][tau: b][T: b x b].
+__host__ __device__ __forceinline__ size_t diamond_elems(int b) { return (size_t)3 * b * b + b; }
+__host__ __device__ __forceinline__ size_t diamond_index(int Q, int j, int k) {
+  return (size_t)j * (Q + 1) - (size_t)j * (j - 1) / 2 + k;
+}
+
+// dlarfg on x[0..len) (shared): v[0] = 1, v[i] = x[i] / (alpha - beta); returns tau, beta in out[0..1].
+__device__ void house(const double* x, int len, double* v, double* out, int b) {
+  const int t = threadIdx.x;
+  if (t < 32) {
+    double s = 0.0;
+    for (int i = 1 + t; i < len; i += 32) s += x[i] * x[i];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (t == 0) {
+      double alpha = x[0], tt = 0.0, sl = 0.0, be = alpha;
+      if (s > 0.0) {
+        be = -copysign(sqrt(alpha * alpha + s), alpha);
+        tt = (be - alpha) / be;
+        sl = 1.0 / (alpha - be);
+      }
+      out[0] = tt;
+      out[1] = be;
+      out[2] = sl;
+    }
+  }
+  __syncthreads();
+  double sl = out[2];
+  for (int i = t; i < b; i += blockDim.x) v[i] = (i == 0) ? 1.0 : (i < len ? x[i] * sl : 0.0);
+  __syncthreads();
+}
+
+// D (len x len, full, ld BMAX+1) <- H D H, H = I - tau v v^T.
+__device__ void two_sided(double* D, int len, const double* v, double tau, double* p, double* red) {
+  const int t = threadIdx.x, i = t & 63, part = t >> 6;
+  double s = 0.0;
+  if (i < len)
+    for (int q = part; q < len; q += 4) s += D[i * (BMAX + 1) + q] * v[q];
+  red[part * BMAX + i] = s;
+  __syncthreads();
+  if (t < len) p[t] = tau * (red[t] + red[BMAX + t] + red[2 * BMAX + t] + red[3 * BMAX + t]);
+  __syncthreads();
+  if (t < 32) {  // K = tau/2 p^T v
+    double k = 0.0;
+    for (int q = t; q < len; q += 32) k += p[q] * v[q];
+    for (int o = 16; o; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+    if (t == 0) red[4 * BMAX] = 0.5 * tau * k;
+  }
+  __syncthreads();
+  double K = red[4 * BMAX];
+  if (t < len) p[t] -= K * v[t];  // w
+  __syncthreads();
+  for (int idx = t; idx < len * len; idx += blockDim.x) {
+    int a = idx % len, c = idx / len;
+    D[a * (BMAX + 1) + c] -= v[a] * p[c] + p[a] * v[c];
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_bulge(BulgeArgs a) {
+  extern __shared__ double sm[];
+  double* Bm = sm;                          // BMAX x (BMAX+1), [row][col]
+  double* Dm = Bm + BMAX * (BMAX + 1);
+  double* vp = Dm + BMAX * (BMAX + 1);      // previous reflector
+  double* vc = vp + BMAX;                   // current reflector
+  double* xv = vc + BMAX;                   // column to annihilate / scratch
+  double* pw = xv + BMAX;
+  double* red = pw + BMAX;                  // 4*BMAX + 1
+  double* hs = red + 4 * BMAX + 8;          // tau, beta, scale
+  __shared__ int abort_flag;
+  const int t = threadIdx.x, M = a.M, b = a.b, ldab = a.ldab;
+  if (t == 0) abort_flag = 0;
+  __syncthreads();
+  if (status_bad(a.st)) return;
+  for (int s = blockIdx.x; s <= M - 2; s += gridDim.x) {
+    const int ns = bulge_steps(M, b, s);
+    double taup = 0.0;
+    for (int k = 0; k < ns; ++k) {
+      if (s > 0 && t == 0) {  // step k of sweep s needs step k+1 of sweep s-1
+        int pns = bulge_steps(M, b, s - 1);
+        int need = k + 2 < pns ? k + 2 : pns;
+        unsigned long long t0 = gclock();
+        while (ld_acquire(a.prog + (s - 1)) < need) {
+          if (*(volatile int*)(a.st + 1) != 0) { abort_flag = 1; break; }
+          if (gclock() - t0 > 4000000000ull) {
+            atomicExch(a.st + 1, GEP_ERR_TIMEOUT);
+            abort_flag = 1;
+            break;
+          }
+          __nanosleep(100);
+        }
+      }
+      __syncthreads();
+      if (abort_flag) return;
+      const int st_k = s + 1 + k * b;
+      const int len = (M - st_k) < b ? (M - st_k) : b;
+      if (k == 0) {
+        for (int i = t; i < len; i += blockDim.x) xv[i] = __ldcg(a.AB + (1 + i) + (size_t)s * ldab);
+        __syncthreads();
+        house(xv, len, vc, hs, b);
+        if (t < len) a.AB[(1 + t) + (size_t)s * ldab] = (t == 0) ? hs[1] : 0.0;
+      } else {
+        const int stp = st_k - b;  // previous block's first row/column (its length is b)
+        for (int idx = t; idx < len * b; idx += blockDim.x) {
+          int i = idx % len, q = idx / len;
+          Bm[i * (BMAX + 1) + q] = __ldcg(a.AB + (b + i - q) + (size_t)(stp + q) * ldab);
+        }
+        __syncthreads();
+        {  // B <- B H(s,k-1): y = B vp, B -= taup y vp^T
+          int i = t & 63, part = t >> 6;
+          double y = 0.0;
+          if (i < len)
+            for (int q = part; q < b; q += 4) y += Bm[i * (BMAX + 1) + q] * vp[q];
+          red[part * BMAX + i] = y;
+          __syncthreads();
+          if (t < len) pw[t] = taup * (red[t] + red[BMAX + t] + red[2 * BMAX + t] + red[3 * BMAX + t]);
+          __syncthreads();
+          for (int idx = t; idx < len * b; idx += blockDim.x) {
+            int ii = idx % len, q = idx / len;
+            Bm[ii * (BMAX + 1) + q] -= pw[ii] * vp[q];
+          }
+          __syncthreads();
+        }
+        for (int i = t; i < len; i += blockDim.x) xv[i] = Bm[i * (BMAX + 1)];
+        __syncthreads();
+        house(xv, len, vc, hs, b);
+        {  // B(:, 1:) <- H B(:, 1:): u = tau B^T v
+          double tk = hs[0];
+          int q = t & 63, part = t >> 6;
+          double u = 0.0;
+          if (q >= 1 && q < b)
+            for (int i = part; i < len; i += 4) u += vc[i] * Bm[i * (BMAX + 1) + q];
+          red[part * BMAX + q] = u;
+          __syncthreads();
+          if (t < b) pw[t] = tk * (red[t] + red[BMAX + t] + red[2 * BMAX + t] + red[3 * BMAX + t]);
+          __syncthreads();
+          for (int idx = t; idx < len * b; idx += blockDim.x) {
+            int i = idx % len, qq = idx / len;
+            double x;
+            if (qq == 0) x = (i == 0) ? hs[1] : 0.0;
+            else x = Bm[i * (BMAX + 1) + qq] - vc[i] * pw[qq];
+            a.AB[(b + i - qq) + (size_t)(stp + qq) * ldab] = x;
+          }
+        }
+      }
+      // D = C(st_k : st_k+len, same) <- H D H
+      for (int idx = t; idx < len * len; idx += blockDim.x) {
+        int i = idx % len, q = idx / len;
+        int lo = i > q ? i : q, hi = i > q ? q : i;
+        Dm[i * (BMAX + 1) + q] = __ldcg(a.AB + (lo - hi) + (size_t)(st_k + hi) * ldab);
+      }
+      __syncthreads();
+      double tk = hs[0];
+      two_sided(Dm, len, vc, tk, pw, red);
+      for (int idx = t; idx < len * len; idx += blockDim.x) {
+        int i = idx % len, q = idx / len;
+        if (i >= q) a.AB[(i - q) + (size_t)(st_k + q) * ldab] = Dm[i * (BMAX + 1) + q];
+      }
+      if (a.q2) {  // reflector into diamond (j, k), column c
+        int j = s / b, c = s - j * b;
+        double* D0 = a.q2 + diamond_index(a.Q, j, k) * diamond_elems(b);
+        for (int i = t; i < len; i += blockDim.x) D0[(c + i) + (size_t)c * 2 * b] = vc[i];
+        if (t == 0) D0[(size_t)2 * b * b + c] = tk;
+      }
+      if (t < b) vp[t] = vc[t];
+      taup = tk;
+      __threadfence();
+      __syncthreads();
+      if (t == 0) st_release(a.prog + s, k + 1);
+    }
+  }
+}
+
+__global__ void k_band_diag(int M, const double* __restrict__ AB, int ldab, double* __restrict__ d,
+                            double* __restrict__ e, const int* st) {
+  if (status_bad(st)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  d[i] = AB[(size_t)i * ldab];
+  if (i + 1 < M) e[i] = AB[1 + (size_t)i * ldab];
+}
+
+// ------------------------------------------------------------------ Q2 application
+
+constexpr int Q2_COLS = 64;  // Z columns per CTA
+
+// Z <- G(j,k) Z for every diamond of wavefront t (blockIdx.x) on a slab of Q2_COLS
+// columns (blockIdx.y).  G(j,k) = H(s0,k) ... H(s0+b-1,k) is applied reflector by
+// reflector, the last one first.  Each Z column is owned by four lanes of one warp.
+__global__ void __launch_bounds__(256) k_q2_apply(int M, int b, int Q, int wt, const double* __restrict__ q2,
+                                                  double* __restrict__ Z, int ldz, int ncol, const int* st) {
+  extern __shared__ double sm[];
+  if (status_bad(st)) return;
+  const int kmin = wt - Q > 0 ? wt - Q : 0;
+  const int k = kmin + blockIdx.x;
+  if (2 * k > wt) return;  // k <= wt / 2 keeps j + k <= Q
+  const int j = Q - wt + k;
+  if (j < 0 || j > Q || k > Q - j) return;
+  const int L = 2 * b - 1;
+  const int r0 = 1 + (j + k) * b;
+  const int c0 = blockIdx.y * Q2_COLS;
+  double* Vs = sm;                      // [c][2b]
+  double* Zs = Vs + (size_t)2 * b * b;  // [row][Q2_COLS + 1]
+  double* ts = Zs + (size_t)L * (Q2_COLS + 1);
+  const double* D0 = q2 + diamond_index(Q, j, k) * diamond_elems(b);
+  const int t = threadIdx.x;
+  for (int idx = t; idx < 2 * b * b; idx += blockDim.x) Vs[idx] = D0[idx];
+  if (t < b) ts[t] = D0[(size_t)2 * b * b + t];
+  for (int idx = t; idx < L * Q2_COLS; idx += blockDim.x) {
+    int r = idx % L, cc = idx / L;
+    int gr = r0 + r, gc = c0 + cc;
+    Zs[r * (Q2_COLS + 1) + cc] = (gr < M && gc < ncol) ? Z[gr + (size_t)gc * ldz] : 0.0;
+  }
+  __syncthreads();
+  const int col = t >> 2, part = t & 3;
+  for (int c = b - 1; c >= 0; --c) {
+    double tc = ts[c];
+    if (tc == 0.0) continue;
+    const double* v = Vs + (size_t)c * 2 * b;
+    double u = 0.0;
+    for (int r = c + part; r < c + b; r += 4) u += v[r] * Zs[r * (Q2_COLS + 1) + col];
+    u += __shfl_xor_sync(0xffffffffu, u, 1);
+    u += __shfl_xor_sync(0xffffffffu, u, 2);
+    u *= tc;
+    for (int r = c + part; r < c + b; r += 4) Zs[r * (Q2_COLS + 1) + col] -= u * v[r];
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int idx = t; idx < L * Q2_COLS; idx += blockDim.x) {
+    int r = idx % L, cc = idx / L;
+    int gr = r0 + r, gc = c0 + cc;
+    if (gr < M && gc < ncol) Z[gr + (size_t)gc * ldz] = Zs[r * (Q2_COLS + 1) + cc];
+  }
+}
+
+size_t q2_smem_bytes(int b) {
+  return ((size_t)2 * b * b + (size_t)(2 * b - 1) * (Q2_COLS + 1) + b) * sizeof(double);
+}
+size_t bulge_smem_bytes() { return ((size_t)2 * BMAX * (BMAX + 1) + 4 * BMAX + 4 * BMAX + 16) * sizeof(double); }
+
+}  // namespace
+
+size_t q2_elems(int M, int b) {
+  if (M < 2 || b < 1) return 0;
+  size_t Q = (size_t)(M - 2) / b;
+  return (Q + 1) * (Q + 2) / 2 * diamond_elems(b);
+}
+
+size_t band_ws_elems(int M, int b) {
+  size_t G = ((size_t)M + PQ_ROWS - 1) / PQ_ROWS;
+  size_t reduce = 2 * rr(G * BMAX) + 2 * rr(BMAX) + 2 * rr((size_t)M * b) + rr((size_t)M * 3 * b) +
+                  5 * rr((size_t)b * b);
+  size_t chase = rr((size_t)2 * b * M) + rr((size_t)M);  // band + progress counters
+  return reduce > chase ? reduce : chase;
+}
+
+// S1b.  C (M x M, lower on entry) -> band of width b in C (lower), reflectors below the
+// band, tau1[j] for columns j < M - b (zero where no reflector).
+int band_reduce(gep_handle_t h, int M, double* C, int ldc, int b, double* tau1, double* ws, size_t ws_elems,
+                int eng) {
+  if (b < 1 || b > BMAX) return GEP_ERR_UNSUPPORTED;
+  if (ws_elems < band_ws_elems(M, b)) return GEP_ERR_ALLOC;
+  if (M <= 0) return GEP_OK;
+  GEP_CHECK(set_matrix(h, M, 1, 0.0, 0.0, tau1, M));
+  if (M <= b + 1) return GEP_OK;
+  GEP_CHECK(symmetrize_lower(h, M, C, ldc));
+  size_t Gmax = ((size_t)M + PQ_ROWS - 1) / PQ_ROWS;
+  double* part0 = ws;
+  double* part1 = part0 + rr(Gmax * BMAX);
+  double* prow0 = part1 + rr(Gmax * BMAX);
+  double* prow1 = prow0 + rr(BMAX);
+  double* V = prow1 + rr(BMAX);
+  double* CV = V + rr((size_t)M * b);
+  double* WVW = CV + rr((size_t)M * b);
+  double* GV = WVW + rr((size_t)M * 3 * b);
+  double* T = GV + rr((size_t)b * b);
+  double* Tt = T + rr((size_t)b * b);
+  double* Pm = Tt + rr((size_t)b * b);
+  double* Ym = Pm + rr((size_t)b * b);
+  for (int pb = 0; M - pb - b >= 2; pb += b) {
+    const int n = M - pb - b;
+    double* P = C + (pb + b) + (size_t)pb * ldc;
+    const int G = (n + PQ_ROWS - 1) / PQ_ROWS;
+    const int nref = n < b ? n : b;
+    double *pin = part0, *pout = part1, *rin = prow0, *rout = prow1;
+    k_pqr_step<<<G, PQ_ROWS, 0, h->stream>>>(n, b, -1, P, ldc, pin, rin, pout, rout, tau1 + pb, h->d_status);
+    GEP_CHECK(check_launch(h));
+    for (int c = 0; c < nref; ++c) {
+      double* tp = pin; pin = pout; pout = tp;
+      tp = rin; rin = rout; rout = tp;
+      k_pqr_step<<<G, PQ_ROWS, 0, h->stream>>>(n, b, c, P, ldc, pin, rin, pout, rout, tau1 + pb, h->d_status);
+      GEP_CHECK(check_launch(h));
+    }
+    k_panel_v<<<dim3((n + 255) / 256, b), 256, 0, h->stream>>>(n, b, P, ldc, V, h->d_status);
+    GEP_CHECK(check_launch(h));
+    GEP_CHECK(dgemm(h, 'T', 'N', 'F', b, b, n, 1.0, V, n, V, n, 0.0, GV, b, eng));
+    GEP_CHECK(larft_rec(h, b, GV, b, tau1 + pb, T, b, Tt));
+    double* C22 = C + (pb + b) + (size_t)(pb + b) * ldc;
+    double* W = WVW;
+    GEP_CHECK(dgemm(h, 'N', 'N', 'F', n, b, n, 1.0, C22, ldc, V, n, 0.0, CV, n, eng));   // C22 V
+    GEP_CHECK(dgemm(h, 'N', 'N', 'F', n, b, b, 1.0, CV, n, T, b, 0.0, W, n, eng));       // X = C22 V T
+    GEP_CHECK(dgemm(h, 'T', 'N', 'F', b, b, n, 1.0, V, n, W, n, 0.0, Pm, b, eng));       // V^T X
+    GEP_CHECK(dgemm(h, 'T', 'N', 'F', b, b, b, 1.0, T, b, Pm, b, 0.0, Ym, b, eng));      // T^T V^T X
+    GEP_CHECK(dgemm(h, 'N', 'N', 'F', n, b, b, -0.5, V, n, Ym, b, 1.0, W, n, eng));      // W
+    GEP_CHECK(copy_matrix(h, n, b, V, n, WVW + (size_t)n * b, n));
+    GEP_CHECK(copy_matrix(h, n, b, W, n, WVW + (size_t)2 * n * b, n));
+    // C22 -= [W V] [V W]^T = W V^T + V W^T (both triangles: C stays symmetric)
+    GEP_CHECK(dgemm(h, 'N', 'T', 'F', n, n, 2 * b, -1.0, WVW, n, WVW + (size_t)n * b, n, 1.0, C22, ldc, eng));
+  }
+  return GEP_OK;
+}
+
+// S1c.  Band of width b in the lower triangle of C -> d, e; reflectors into q2 (may be null).
+int band_to_tridiag(gep_handle_t h, int M, const double* C, int ldc, int b, double* d, double* e, double* q2,
+                    double* ws, size_t ws_elems) {
+  if (b < 1 || b > BMAX) return GEP_ERR_UNSUPPORTED;
+  if (ws_elems < band_ws_elems(M, b)) return GEP_ERR_ALLOC;
+  if (M <= 0) return GEP_OK;
+  const int ldab = 2 * b;
+  double* AB = ws;
+  int* prog = reinterpret_cast<int*>(ws + rr((size_t)2 * b * M));
+  k_band_copy<<<M, ldab, 0, h->stream>>>(M, b, C, ldc, AB, ldab, h->d_status);
+  GEP_CHECK(check_launch(h));
+  if (M >= 2) {
+    GEP_CUDA(cudaMemsetAsync(prog, 0, sizeof(int) * (size_t)M, h->stream));
+    const int Q = (M - 2) / b;
+    if (q2) GEP_CUDA(cudaMemsetAsync(q2, 0, q2_elems(M, b) * sizeof(double), h->stream));
+    size_t smem = bulge_smem_bytes();
+    static int attr_done = 0;
+    if (!attr_done) {
+      GEP_CUDA(cudaFuncSetAttribute(k_bulge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr_done = 1;
+    }
+    int per_sm = 0;
+    GEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bulge, 256, smem));
+    if (per_sm < 1) return GEP_ERR_UNSUPPORTED;
+    int grid = per_sm * h->sm_count;
+    if (grid > M - 1) grid = M - 1;
+    BulgeArgs a;
+    a.M = M; a.b = b; a.ldab = ldab; a.Q = Q; a.AB = AB; a.prog = prog; a.q2 = q2; a.st = h->d_status;
+    void* args[] = {&a};
+    GEP_CUDA(cudaLaunchCooperativeKernel((void*)k_bulge, dim3(grid), dim3(256), args, smem, h->stream));
+    GEP_CHECK(check_launch(h));
+  }
+  k_band_diag<<<(M + 255) / 256, 256, 0, h->stream>>>(M, AB, ldab, d, e, h->d_status);
+  return check_launch(h);
+}
+
+// Z (M x ncol) <- Q2 Z.
+int apply_q2(gep_handle_t h, int M, int b, const double* q2, double* Z, int ldz, int ncol) {
+  if (b < 1 || b > BMAX) return GEP_ERR_UNSUPPORTED;
+  if (M < 3 || ncol <= 0) return GEP_OK;  // M = 2: the only reflector is the identity
+  const int Q = (M - 2) / b;
+  size_t smem = q2_smem_bytes(b);
+  static int attr_done = 0;
+  if (!attr_done) {
+    GEP_CUDA(cudaFuncSetAttribute(k_q2_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)q2_smem_bytes(BMAX)));
+    attr_done = 1;
+  }
+  const int slabs = (ncol + Q2_COLS - 1) / Q2_COLS;
+  for (int wt = 0; wt <= 2 * Q; ++wt) {
+    int kmin = wt - Q > 0 ? wt - Q : 0, kmax = wt / 2;
+    if (kmax < kmin) continue;
+    k_q2_apply<<<dim3(kmax - kmin + 1, slabs), 256, smem, h->stream>>>(M, b, Q, wt, q2, Z, ldz, ncol,
+                                                                      h->d_status);
+    GEP_CHECK(check_launch(h));
+  }
+  return GEP_OK;
+}
+
+}  // namespace gep

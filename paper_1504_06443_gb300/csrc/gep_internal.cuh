@@ -131,7 +131,18 @@ int tridiag_1stage(gep_handle_t h, int M, double* C, int ldc, double* d, double*
                    double* ws, size_t ws_elems, int engine);
 size_t tridiag_ws_elems(int M);
 int backtransform_q(gep_handle_t h, int M, int ncol, const double* C, int ldc, const double* tau,
-                    double* Z, int ldz, double* ws, size_t ws_elems, int engine);
+                    double* Z, int ldz, double* ws, size_t ws_elems, int engine, int off = 1);
+// T (nb x nb, upper) of the block reflector whose Gram matrix is G = V^T V (backtrans.cu).
+int larft_rec(gep_handle_t h, int nb, const double* G, int ldg, const double* tau, double* T, int ldt,
+              double* tmp);
+// two-stage SEP path (band.cu)
+size_t q2_elems(int M, int b);
+size_t band_ws_elems(int M, int b);
+int band_reduce(gep_handle_t h, int M, double* C, int ldc, int b, double* tau1, double* ws, size_t ws_elems,
+                int eng);
+int band_to_tridiag(gep_handle_t h, int M, const double* C, int ldc, int b, double* d, double* e, double* q2,
+                    double* ws, size_t ws_elems);
+int apply_q2(gep_handle_t h, int M, int b, const double* q2, double* Z, int ldz, int ncol);
 size_t backtransform_ws_elems(int M, int ncol);
 int tridiag_eig_dc(gep_handle_t h, int M, const double* d, const double* e, double* w, double* Z,
                    int ldz, double* ws, size_t ws_elems, int engine);

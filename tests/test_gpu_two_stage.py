@@ -1,0 +1,148 @@
+"""Two-stage SEP path (full -> band -> tridiagonal, bulge-chasing back-transformation)
+against the FP64 oracle.
+
+The tridiagonal T and the band matrix are not unique (they depend on the reflectors
+chosen), so parity is checked on what is: the spectrum of T and of the band equal the
+oracle's spectrum of C, and the back-transformed eigenvectors satisfy C Z = Z Lambda and
+Z^T Z = I.  End to end, gep_solve with sep='2stage' meets the same FP64 bounds as the
+1-stage path, and the two SEP variants agree (the paper's workflows all solve the same
+GEP).  Sizes cover one band, several bands with a ragged tail, M <= b + 1 (already
+banded), odd and minimal bandwidths.
+"""
+import numpy as np
+import pytest
+
+import gep_inputs as gi
+
+pytestmark = pytest.mark.gpu
+
+EPS = 2.0 ** -52
+
+
+@pytest.fixture(scope="module")
+def gep():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1504_06443_gb300 import build
+    build.build()
+    import paper_1504_06443_gb300 as g
+    g.load()
+    return g
+
+
+def dev(x):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def oracle_eigs(oracle_lib, C):
+    M = C.shape[0]
+    w, _, info = oracle_lib.gep_solve(C, np.eye(M), want_vectors=False)
+    assert info == 0
+    return np.sort(w)
+
+
+def band_part(C, b):
+    L = np.tril(C) - np.tril(C, -b - 1)
+    return L + np.tril(L, -1).T
+
+
+@pytest.mark.parametrize("M,b", [(1, 8), (2, 8), (3, 2), (9, 8), (10, 8), (64, 64), (65, 64), (66, 64),
+                                 (200, 8), (200, 64), (300, 7), (513, 32), (600, 64), (257, 1)])
+def test_tridiag_2stage_spectrum(gep, oracle_lib, M, b):
+    C = gi.random_symmetric(M, seed=M + 17 * b)
+    w_ref = oracle_eigs(oracle_lib, C)
+    d, e, tau1, q2, Cb = gep.tridiag_2stage(dev(C), b=b)
+    dh, eh = host(d), host(e)
+    # spectrum of T: Sturm bisection in the oracle, on the GPU's (d, e)
+    wT = np.sort(oracle_lib.bisect(dh, eh)) if M > 0 else dh
+    nC = max(np.max(np.abs(w_ref)), 1.0)
+    assert np.max(np.abs(wT - w_ref)) <= 200 * M * EPS * nC
+    # the band left in C after stage 1 has the same spectrum
+    wB = oracle_eigs(oracle_lib, band_part(host(Cb), b))
+    assert np.max(np.abs(wB - w_ref)) <= 200 * M * EPS * nC
+    # trace invariant
+    assert abs(dh.sum() - np.trace(C)) <= 100 * M * EPS * nC
+
+
+@pytest.mark.parametrize("M,b", [(3, 2), (66, 64), (200, 8), (300, 7), (513, 32), (600, 64)])
+def test_backtransform_2stage(gep, oracle_lib, M, b):
+    C = gi.random_symmetric(M, seed=3 * M + b)
+    d, e, tau1, q2, Cb = gep.tridiag_2stage(dev(C), b=b)
+    dh, eh = host(d), host(e)
+    # eigenvectors of T from the oracle's implicit QL
+    lam, ZT, st = oracle_lib.tql(dh, eh, np.eye(M))
+    assert st == 0
+    Z = host(gep.sep_backtransform_2stage(Cb, tau1, q2, b, dev(ZT)))
+    nC = np.linalg.norm(C)
+    res = np.linalg.norm(C @ Z - Z * lam[None, :]) / (nC * M)
+    orth = np.max(np.abs(Z.T @ Z - np.eye(M)))
+    assert res <= 1e-14, res
+    assert orth <= 1e-12, orth
+
+
+def test_backtransform_2stage_partial_columns(gep, oracle_lib):
+    """ncol < M and a ragged column slab: Q Z for an arbitrary Z equals the product of
+    the two transformations applied column block by column block."""
+    M, b = 333, 16
+    C = gi.random_symmetric(M, seed=5)
+    d, e, tau1, q2, Cb = gep.tridiag_2stage(dev(C), b=b)
+    rng = np.random.default_rng(1)
+    Z = rng.standard_normal((M, 70))
+    full = host(gep.sep_backtransform_2stage(Cb, tau1, q2, b, dev(Z)))
+    part = host(gep.sep_backtransform_2stage(Cb, tau1, q2, b, dev(Z[:, 3:40])))
+    assert np.max(np.abs(full[:, 3:40] - part)) <= 1e-13 * np.max(np.abs(full))
+    # orthogonal: norms preserved
+    assert np.max(np.abs(np.linalg.norm(full, axis=0) - np.linalg.norm(Z, axis=0))) <= 1e-12 * np.sqrt(M)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp64_emulated", "mixed_refined"])
+@pytest.mark.parametrize("reducer", ["twosided", "explicit_inv"])
+def test_solve_2stage_tight_binding(gep, oracle_lib, precision, reducer):
+    M = 516
+    tb = gi.tight_binding(M, seed=M + 7)
+    A, B = tb["A"], tb["B"]
+    w_ref, _, info = oracle_lib.gep_solve(A, B)
+    assert info == 0
+    w, Y, info = gep.solve(dev(A), dev(B), sep="2stage", reducer=reducer, precision=precision)
+    assert info == 0
+    wh, Yh = host(w), host(Y)
+    nA = float(np.max(np.abs(np.linalg.eigvalsh(A))))
+    assert np.max(np.abs(wh - w_ref)) <= 1e-11 * nA
+    res = np.linalg.norm(A @ Yh - (B @ Yh) * wh[None, :]) / (np.linalg.norm(A) * M)
+    orth = np.max(np.abs(Yh.T @ B @ Yh - np.eye(M)))
+    assert res <= 1e-13, res
+    assert orth <= 1e-12, orth
+
+
+@pytest.mark.parametrize("M,b", [(512, 64), (257, 32), (130, 1)])
+def test_solve_2stage_known_spectrum(gep, M, b):
+    g = gi.known_spectrum(M, seed=4)
+    w, Y, info = gep.solve(dev(g["A"]), dev(g["B"]), sep="2stage", bandwidth=b)
+    assert info == 0
+    assert np.max(np.abs(host(w) - np.sort(g["lam"]))) <= 1e-11 * 20.0
+
+
+def test_solve_2stage_values_only_matches_1stage(gep):
+    M = 700
+    tb = gi.tight_binding(M, seed=3)
+    A, B = dev(tb["A"]), dev(tb["B"])
+    w1, _, i1 = gep.solve(A, B, want_vectors=False)
+    w2, _, i2 = gep.solve(A, B, want_vectors=False, sep="2stage", precision="fp64_emulated")
+    w3, Y3, i3 = gep.solve(A, B, sep="2stage", bandwidth=24)
+    assert i1 == i2 == i3 == 0
+    nA = float(np.max(np.abs(host(w1))))
+    assert np.max(np.abs(host(w1) - host(w2))) <= 1e-11 * nA
+    assert np.max(np.abs(host(w1) - host(w3))) <= 1e-11 * nA
+
+
+def test_2stage_rejects_bad_bandwidth(gep):
+    A = dev(np.eye(8))
+    with pytest.raises(gep.GepError):
+        gep.solve(A, A, sep="2stage", bandwidth=65)
+    with pytest.raises(gep.GepError):
+        gep.tridiag_2stage(A, b=0)
