@@ -38,6 +38,10 @@ def parse():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--precision", default="fp64_emulated", choices=["fp64_emulated", "fp64", "mixed_refined"])
     p.add_argument("--reducer", default="twosided", choices=["twosided", "explicit_inv"])
+    p.add_argument("--sep", default="1stage", choices=["1stage", "2stage"],
+                   help="SEP reduction: 1-stage tridiagonalisation or full->band->tridiagonal")
+    p.add_argument("--bandwidth", type=int, default=0, help="band width of --sep 2stage (0: library default 64)")
+    p.add_argument("--values-only", action="store_true", help="eigenvalues only (T_evo of the paper's benchmark)")
     p.add_argument("--cpu-sample-M", type=int, default=2048)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -405,11 +409,13 @@ def main():
     B = torch.as_tensor(tb["B"]).to("cuda")
     if a.no_e2e:
         del tb
+    vectors = not a.values_only
+    sopts = dict(reducer=a.reducer, sep=a.sep, bandwidth=a.bandwidth, precision=a.precision, want_vectors=vectors)
     w = torch.empty(M, dtype=torch.float64, device="cuda")
-    Yt = torch.empty((M, M), dtype=torch.float64, device="cuda")
+    Yt = torch.empty((M, M), dtype=torch.float64, device="cuda") if vectors else None
     h = gep.default_handle()
-    opts = gep.make_options(reducer=a.reducer, precision=a.precision, timers=True)
-    h.ensure_workspace(gep.workspace_bytes(M, handle=h, reducer=a.reducer, precision=a.precision, timers=True))
+    opts = gep.make_options(timers=True, **sopts)
+    h.ensure_workspace(gep.workspace_bytes(M, handle=h, timers=True, **sopts))
     stream = torch.cuda.current_stream()
 
     for _ in range(a.warmup):
@@ -438,6 +444,7 @@ def main():
     prof = h.profile_read(reset=True)
     h.profile_enable(0)
     stages = h.stage_times()
+    band_ms = h.band_times() if a.sep == "2stage" else None
     info = max(info, h.info())
     t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if dist:
@@ -445,7 +452,7 @@ def main():
     ms_max = t_local.item()
 
     check = None
-    if not a.no_check:
+    if not a.no_check and vectors:
         check = sampled_check(A, B, w, Yt.t(), 64, seed)
 
     e2e = None
@@ -454,12 +461,12 @@ def main():
         Bh = torch.from_numpy(tb["B"]).pin_memory()
         del tb
         wh = torch.empty(M, dtype=torch.float64).pin_memory()
-        Yh = torch.empty((M, M), dtype=torch.float64).pin_memory()
+        Yh = torch.empty((M, M), dtype=torch.float64).pin_memory() if vectors else None
         del Yt
         torch.cuda.empty_cache()
         hh = gep.Handle()
         import ctypes
-        o = gep.make_options(reducer=a.reducer, precision=a.precision)
+        o = gep.make_options(**sopts)
         nb = ctypes.c_size_t()
         hh.lib.gep_workspace_size_host(hh.h, M, ctypes.byref(o), ctypes.byref(nb))
         h.ws = None
@@ -469,9 +476,10 @@ def main():
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         rc = hh.lib.gep_solve_host(hh.h, M, P(Ah.data_ptr()), M, P(Bh.data_ptr()), M, P(wh.data_ptr()),
-                                   P(Yh.data_ptr()), M, ctypes.byref(o))
+                                   P(Yh.data_ptr() if vectors else 0), M, ctypes.byref(o))
         e2e_s = time.perf_counter() - t1
-        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 2 * 8 * M * M, "d2h_bytes_per_step": 8 * M + 8 * M * M,
+        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 2 * 8 * M * M,
+               "d2h_bytes_per_step": 8 * M + (8 * M * M if vectors else 0),
                "rc": rc, "max_abs_dw_vs_device": float((wh.cuda() - w).abs().max().item())}
 
     pk, pk_kind = peaks()
@@ -496,18 +504,22 @@ def main():
                "sample": f"oracle full GEP solve of the M={a.cpu_sample_M} tight-binding pencil "
                          f"({a.cpu_sample_M // 4} atoms) took {dt:.2f} s; scaled by (M/{a.cpu_sample_M})^3"}
 
-    flops_alg = (1.0 / 3 + 2.0 + 4.0 / 3 + 8.0 / 3 + 2.0 + 1.0) * float(M) ** 3
+    flops_alg = ((1.0 / 3 + 2.0 + 4.0 / 3 + 8.0 / 3 + 2.0 + 1.0) if vectors else (1.0 / 3 + 2.0 + 4.0 / 3)) * float(M) ** 3
     if rank == 0:
         line = {"metric": METRIC, "value": ms_max / 1e3, "unit": "s", "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"tight-binding GEP M={M} ({M // 4} atoms x 4 sp orbitals), all eigenpairs",
-                           "M": M, "seed": a.seed, "reducer": a.reducer, "sep": "1stage",
+                "config": {"workload": f"tight-binding GEP M={M} ({M // 4} atoms x 4 sp orbitals), "
+                                       + ("all eigenpairs" if vectors else "all eigenvalues"),
+                           "M": M, "seed": a.seed, "reducer": a.reducer, "sep": a.sep,
+                           "bandwidth": (a.bandwidth or 64) if a.sep == "2stage" else None,
                            "precision": a.precision, "parallelism": "replicas" if world > 1 else "single",
                            "l2": "inputs larger than L2 (8.6 GB per matrix at M=32768)",
                            "generator_s": round(gen_s, 2)},
                 "stage_ms": dict(zip(["R1_cholesky", "R2_reduce", "S1_tridiag", "S2_dc", "S3_back_q",
                                       "R3_backsub", "MP3_refine"], [round(x, 2) for x in stages])),
+                "band_ms": dict(zip(["S1b_full_to_band", "S1c_bulge_chasing"], [round(x, 2) for x in band_ms]))
+                if band_ms else None,
                 "info": info, "gpu_launches": int(launches),
                 "fp64_equiv_tflops_whole_solve": flops_alg / (ms_max * 1e-3) / 1e12,
                 "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "check": check}

@@ -219,6 +219,11 @@ int gep_get_stage_times(gep_handle_t h, double t[7]);
  * library's mixed-precision extension.) */
 int gep_refine_steps(gep_handle_t h);
 
+/* Split of the SEP reduction time t[2] of the last GEP_SEP_2STAGE gep_solve with
+ * timers: t[0] full -> band, t[1] band -> tridiagonal (bulge chasing), in ms.
+ * Synchronises with that solve; GEP_ERR_UNSUPPORTED when none was recorded. */
+int gep_get_band_times(gep_handle_t h, double t[2]);
+
 /* Number of kernels the library launched since gep_create / last reset. */
 long long gep_launch_count(gep_handle_t h, int reset);
 

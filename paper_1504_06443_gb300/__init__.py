@@ -93,6 +93,7 @@ def load():
             "gep_get_stage_times": (_I, [_P, ctypes.POINTER(_D)]),
             "gep_launch_count": (ctypes.c_longlong, [_P, _I]),
             "gep_refine_steps": (_I, [_P]),
+            "gep_get_band_times": (_I, [_P, ctypes.POINTER(_D)]),
             "gep_profile_enable": (_I, [_P, _I]),
             "gep_profile_read": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D),
                                       ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), _I]),
@@ -200,6 +201,12 @@ class Handle:
 
     def launches(self, reset=False):
         return int(self.lib.gep_launch_count(self.h, 1 if reset else 0))
+
+    def band_times(self):
+        """(full->band ms, bulge-chasing ms) of the last two-stage solve with timers."""
+        t = (_D * 2)()
+        _check(self.lib.gep_get_band_times(self.h, t), "gep_get_band_times")
+        return [t[0], t[1]]
 
     def refine_steps(self):
         """FP64 refinement steps the last mixed-precision solve on this handle took."""

@@ -123,6 +123,7 @@ int gep_create(gep_handle_t* out, void* stream) {
     return GEP_ERR_CUDA;
   }
   for (int i = 0; i < 8; ++i) cudaEventCreate(&h->ev[i]);
+  cudaEventCreate(&h->ev_band);
   *out = h;
   return GEP_OK;
 }
@@ -138,6 +139,7 @@ int gep_destroy(gep_handle_t h) {
   if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   cudaFree(h->d_batch_info);
   for (int i = 0; i < 8; ++i) cudaEventDestroy(h->ev[i]);
+  cudaEventDestroy(h->ev_band);
   cudaFree(h->d_status);
   cudaFree(h->d_splitk);
   h->magic = 0;
@@ -255,6 +257,19 @@ int gep_get_stage_times(gep_handle_t h, double t[7]) {
     GEP_CUDA(cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]));
     t[i] = ms;
   }
+  return GEP_OK;
+}
+
+int gep_get_band_times(gep_handle_t h, double t[2]) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (!t) return -2;
+  if (!h->timers_recorded || !h->band_recorded) return GEP_ERR_UNSUPPORTED;
+  GEP_CUDA(cudaEventSynchronize(h->ev[3]));
+  float a = 0.f, b = 0.f;
+  GEP_CUDA(cudaEventElapsedTime(&a, h->ev[2], h->ev_band));
+  GEP_CUDA(cudaEventElapsedTime(&b, h->ev_band, h->ev[3]));
+  t[0] = a;
+  t[1] = b;
   return GEP_OK;
 }
 
@@ -514,9 +529,11 @@ int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, dou
   }
   mark(h, o, 2);
   const int bw = band_of(o);
+  h->band_recorded = two_stage(o) && o->timers;
   double* q2 = (two_stage(o) && o->want_vectors) ? (double*)(base + Ly.q2) : nullptr;
   if (two_stage(o)) {
     GEP_CHECK(band_reduce(h, M, Cw, ldcw, bw, tvec, (double*)uni, Ly.uni_bytes / sizeof(double), eng));   // S1b
+    if (o->timers) cudaEventRecord(h->ev_band, h->stream);
     GEP_CHECK(band_to_tridiag(h, M, Cw, ldcw, bw, dvec, evec, q2, (double*)uni,
                               Ly.uni_bytes / sizeof(double)));  // S1c
   } else {

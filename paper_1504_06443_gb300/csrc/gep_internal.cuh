@@ -21,6 +21,8 @@ struct gep_handle_s {
   int sm_count = 152;
   int magic = 0x6e70;
   cudaEvent_t ev[8] = {};
+  cudaEvent_t ev_band = nullptr;  // between full->band and bulge chasing (two-stage, timers on)
+  bool band_recorded = false;
   bool timers_recorded = false;
   // optional per-launch timing of the tensor-core product kernel
   int prof_on = 0;
