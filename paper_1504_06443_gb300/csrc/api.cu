@@ -38,6 +38,10 @@ size_t union_bytes(int M, const gep_options* o) {
   size_t tri = two_stage(o) ? band_ws_elems(M, band_of(o)) * sizeof(double) : tridiag_ws_elems(M) * sizeof(double);
   size_t dc = o->want_vectors ? dc_ws_bytes(M) : 0;
   size_t bt = o->want_vectors ? backtransform_ws_elems(M, M) * sizeof(double) : 0;
+  if (two_stage(o) && o->want_vectors) {
+    size_t q2t = q2_tile_ws_elems(M, band_of(o)) * sizeof(double);
+    if (q2t > bt) bt = q2t;
+  }
   size_t r3 = o->want_vectors ? (r256(tmpb) + (o->reducer == GEP_RED_EXPLICIT_INV ? r256(mm) : 0)) : 0;
   size_t rf = (o->precision == GEP_PREC_MIXED_REFINED) ? r256(refine_ws_elems(M) * sizeof(double)) : 0;
   size_t u = red;
@@ -463,7 +467,7 @@ int sep_backtransform_2stage(gep_handle_t h, int M, int ncol, int b, const doubl
   size_t n = backtransform_ws_elems(M, ncol);
   double* ws = ar.take<double>(n);
   if (!ar.ok) return GEP_ERR_ALLOC;
-  GEP_CHECK(apply_q2(h, M, b, q2, Z, ldz, ncol));
+  GEP_CHECK(apply_q2(h, M, b, q2, Z, ldz, ncol, GEP_PREC_FP64, nullptr, 0));
   return backtransform_q(h, M, ncol, C, ldc, tau1, Z, ldz, ws, n, GEP_PREC_FP64, b);
 }
 
@@ -552,7 +556,7 @@ int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, dou
   GEP_CHECK(tridiag_eig_dc(h, M, dvec, evec, w, Y, ldy, (double*)uni, Ly.uni_bytes, eng));  // D&C
   mark(h, o, 4);
   if (two_stage(o)) {
-    GEP_CHECK(apply_q2(h, M, bw, q2, Y, ldy, M));
+    GEP_CHECK(apply_q2(h, M, bw, q2, Y, ldy, M, eng, (double*)uni, Ly.uni_bytes / sizeof(double)));
     GEP_CHECK(backtransform_q(h, M, M, Cw, ldcw, tvec, Y, ldy, (double*)uni, Ly.uni_bytes / sizeof(double), eng,
                               bw));
   } else {

@@ -414,6 +414,67 @@ __global__ void __launch_bounds__(256) k_q2_apply(int M, int b, int Q, int wt, c
   }
 }
 
+// Dense tiles of Q2.  Tile (J, K) holds the diamonds (j, k) with j in [J TQ, (J+1) TQ)
+// and k in [K TQ, (K+1) TQ); diamond (j, k) acts on rows 1 + (j + k) b .. + 2b - 2, so
+// the tile acts on the W = 2 TQ b rows starting at 1 + (J + K) TQ b.  A diamond must
+// precede (j, k+1) and, where rows overlap, the diamonds (j-1, k'), k' >= k of the next
+// lower group: every dependency keeps or lowers j and keeps or raises k, so tiles are
+// applied with J descending and K ascending, and inside a tile with j descending and k
+// ascending.  U(J, K) is the product of its diamonds in that order, built by applying
+// them to the identity, W x TB_COLS columns per CTA.
+constexpr int TQ = 4;
+constexpr int TB_COLS = 32;  // tile columns per CTA in the build (8 lanes per column)
+
+__global__ void __launch_bounds__(256) k_q2_tile_build(int M, int b, int Q, int J, const double* __restrict__ q2,
+                                                       double* __restrict__ U, const int* st) {
+  extern __shared__ double sm[];
+  if (status_bad(st)) return;
+  const int K = blockIdx.x;
+  const int W = 2 * TQ * b;
+  const int J0 = J * TQ, K0 = K * TQ;
+  const int r0 = 1 + (J0 + K0) * b;  // global row of tile row 0
+  const int c0 = blockIdx.y * TB_COLS;
+  double* Us = sm;  // [row][TB_COLS + 1]
+  const int t = threadIdx.x;
+  for (int idx = t; idx < W * TB_COLS; idx += blockDim.x) {
+    int r = idx % W, cc = idx / W;
+    Us[r * (TB_COLS + 1) + cc] = (r == c0 + cc) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int col = t >> 3, part = t & 7;
+  const int jhi = min(J0 + TQ - 1, Q);
+  for (int j = jhi; j >= J0; --j) {
+    for (int k = K0; k < K0 + TQ; ++k) {
+      if (k > Q - j) continue;
+      const double* D0 = q2 + diamond_index(Q, j, k) * diamond_elems(b);
+      const int lo = (j + k - J0 - K0) * b;  // tile row of the diamond's row 0
+      for (int c = b - 1; c >= 0; --c) {
+        double tc = D0[(size_t)2 * b * b + c];
+        if (tc == 0.0) continue;
+        const double* v = D0 + (size_t)c * 2 * b;
+        double u = 0.0;
+        for (int r = c + part; r < c + b; r += 8)
+          if (r0 + lo + r < M) u += v[r] * Us[(lo + r) * (TB_COLS + 1) + col];
+        u += __shfl_xor_sync(0xffffffffu, u, 1);
+        u += __shfl_xor_sync(0xffffffffu, u, 2);
+        u += __shfl_xor_sync(0xffffffffu, u, 4);
+        u *= tc;
+        for (int r = c + part; r < c + b; r += 8)
+          if (r0 + lo + r < M) Us[(lo + r) * (TB_COLS + 1) + col] -= u * v[r];
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+  double* Ut = U + (size_t)K * W * W;  // W x W column-major
+  for (int idx = t; idx < W * TB_COLS; idx += blockDim.x) {
+    int r = idx % W, cc = idx / W;
+    if (c0 + cc < W) Ut[r + (size_t)(c0 + cc) * W] = Us[r * (TB_COLS + 1) + cc];
+  }
+}
+
+size_t q2_tile_smem_bytes(int b) { return (size_t)2 * TQ * b * (TB_COLS + 1) * sizeof(double); }
+
 size_t q2_smem_bytes(int b) {
   return ((size_t)2 * b * b + (size_t)(2 * b - 1) * (Q2_COLS + 1) + b) * sizeof(double);
 }
@@ -527,11 +588,50 @@ int band_to_tridiag(gep_handle_t h, int M, const double* C, int ldc, int b, doub
   return check_launch(h);
 }
 
-// Z (M x ncol) <- Q2 Z.
-int apply_q2(gep_handle_t h, int M, int b, const double* q2, double* Z, int ldz, int ncol) {
+size_t q2_tile_ws_elems(int M, int b) {
+  if (M < 3 || b < 1) return 0;
+  size_t Q = (size_t)(M - 2) / b;
+  size_t nK = Q / TQ + 1, W = (size_t)2 * TQ * b;
+  return rr(nK * W * W) + rr(W * (size_t)M);
+}
+
+// Z (M x ncol) <- Q2 Z.  engine FP64: diamonds applied directly on the FP64 cores.
+// Otherwise the diamonds are merged into dense W x W tiles U(J, R) and every tile is
+// applied as one product Z(rows) <- U Z(rows) on the engine (ws: q2_tile_ws_elems).
+int apply_q2(gep_handle_t h, int M, int b, const double* q2, double* Z, int ldz, int ncol, int engine, double* ws,
+             size_t ws_elems) {
   if (b < 1 || b > BMAX) return GEP_ERR_UNSUPPORTED;
   if (M < 3 || ncol <= 0) return GEP_OK;  // M = 2: the only reflector is the identity
   const int Q = (M - 2) / b;
+  if (engine != GEP_PREC_FP64) {
+    if (ws_elems < q2_tile_ws_elems(M, b)) return GEP_ERR_ALLOC;
+    const int W = 2 * TQ * b;
+    const int nJ = Q / TQ + 1;
+    double* U = ws;
+    double* Tmp = ws + rr((size_t)(Q / TQ + 1) * W * W);
+    size_t smem = q2_tile_smem_bytes(b);
+    static int attr_done = 0;
+    if (!attr_done) {
+      GEP_CUDA(cudaFuncSetAttribute(k_q2_tile_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)q2_tile_smem_bytes(BMAX)));
+      attr_done = 1;
+    }
+    for (int J = nJ - 1; J >= 0; --J) {
+      const int nK = (Q - J * TQ) / TQ + 1;  // tiles (J, K) with a diamond: K TQ <= Q - J TQ
+      k_q2_tile_build<<<dim3(nK, (W + TB_COLS - 1) / TB_COLS), 256, smem, h->stream>>>(M, b, Q, J, q2, U,
+                                                                                      h->d_status);
+      GEP_CHECK(check_launch(h));
+      for (int K = 0; K < nK; ++K) {
+        const int r0 = 1 + (J + K) * TQ * b;
+        if (r0 >= M) break;
+        const int Wc = (M - r0) < W ? (M - r0) : W;
+        const double* Ut = U + (size_t)K * W * W;
+        GEP_CHECK(dgemm(h, 'N', 'N', 'F', Wc, ncol, Wc, 1.0, Ut, W, Z + r0, ldz, 0.0, Tmp, Wc, engine));
+        GEP_CHECK(copy_matrix(h, Wc, ncol, Tmp, Wc, Z + r0, ldz));
+      }
+    }
+    return GEP_OK;
+  }
   size_t smem = q2_smem_bytes(b);
   static int attr_done = 0;
   if (!attr_done) {

@@ -144,7 +144,9 @@ int band_reduce(gep_handle_t h, int M, double* C, int ldc, int b, double* tau1, 
                 int eng);
 int band_to_tridiag(gep_handle_t h, int M, const double* C, int ldc, int b, double* d, double* e, double* q2,
                     double* ws, size_t ws_elems);
-int apply_q2(gep_handle_t h, int M, int b, const double* q2, double* Z, int ldz, int ncol);
+size_t q2_tile_ws_elems(int M, int b);
+int apply_q2(gep_handle_t h, int M, int b, const double* q2, double* Z, int ldz, int ncol, int engine, double* ws,
+             size_t ws_elems);
 size_t backtransform_ws_elems(int M, int ncol);
 int tridiag_eig_dc(gep_handle_t h, int M, const double* d, const double* e, double* w, double* Z,
                    int ldz, double* ws, size_t ws_elems, int engine);

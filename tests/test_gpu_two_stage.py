@@ -146,3 +146,23 @@ def test_2stage_rejects_bad_bandwidth(gep):
         gep.solve(A, A, sep="2stage", bandwidth=65)
     with pytest.raises(gep.GepError):
         gep.tridiag_2stage(A, b=0)
+
+
+@pytest.mark.parametrize("M,b,precision", [(1100, 16, "fp64_emulated"), (2100, 64, "fp64_emulated"),
+                                           (776, 8, "mixed_refined")])
+def test_solve_2stage_q2_tiles(gep, oracle_lib, M, b, precision):
+    """Tensor-core engines apply Q2 as dense tiles of 4 x 4 diamonds: many tile rows and
+    columns and a ragged last tile, checked end to end against the oracle."""
+    tb = gi.tight_binding(M, seed=M + 1)
+    A, B = tb["A"], tb["B"]
+    w_ref, _, info = oracle_lib.gep_solve(A, B, want_vectors=False)
+    assert info == 0
+    w, Y, info = gep.solve(dev(A), dev(B), sep="2stage", bandwidth=b, precision=precision)
+    assert info == 0
+    wh, Yh = host(w), host(Y)
+    nA = float(np.max(np.abs(w_ref)))
+    assert np.max(np.abs(wh - w_ref)) <= 1e-11 * nA
+    res = np.linalg.norm(A @ Yh - (B @ Yh) * wh[None, :]) / (np.linalg.norm(A) * M)
+    orth = np.max(np.abs(Yh.T @ B @ Yh - np.eye(M)))
+    assert res <= 1e-13, res
+    assert orth <= 1e-12, orth
