@@ -308,6 +308,10 @@ struct OzArgs {
   int* st;
 };
 
+// SC, LC > 0 fix the plane and level counts at compile time (the two settings the
+// solver uses): the MMA sequence of a k-step is then straight-line code whose
+// descriptors are a per-stage base plus constants.  SC = LC = 0 reads them from p.
+template <int SC, int LC>
 __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__ CUtensorMap tmA,
                                                           const __grid_constant__ CUtensorMap tmB, OzArgs p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -318,7 +322,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__
   __shared__ int skip;
   if (p.lower && tm + TM - 1 < tn) return;  // tile strictly above the diagonal (uniform)
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int S = p.S, LMAX = p.lmax;
+  const int S = SC > 0 ? SC : p.S, LMAX = LC > 0 ? LC : p.lmax;
   const uint32_t a_bytes = (uint32_t)S * TM * TK * 2, b_bytes = (uint32_t)S * TN * TK * 2;
   const uint32_t stage_bytes = a_bytes + b_bytes;
   const uint32_t bar_full = smem_u32(&bars[0]), bar_empty = smem_u32(&bars[STAGES]);
@@ -388,18 +392,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__
           if (!ok) break;
           tc_fence_after();
           uint32_t abase = smem_u32(smem + (size_t)sidx * stage_bytes);
-          uint32_t bbase = abase + a_bytes;
-#pragma unroll 1
+          const uint64_t a0 = sdesc_sw64(abase), b0 = sdesc_sw64(abase + a_bytes);
+#pragma unroll
           for (int kk = 0; kk < TK / 16; ++kk) {
-            for (int s = 1; s <= S; ++s) {
-              int tmax = min(S, LMAX - s);
+#pragma unroll
+            for (int s = 1; s <= MAXS; ++s) {
+              if (s > S) break;
+              const int tmax = min(S, LMAX - s);
               if (tmax < 1) break;
-              uint64_t adesc = sdesc_sw64(abase + (uint32_t)(s - 1) * TM * TK * 2 + kk * 32);
-              for (int t0 = 1; t0 <= tmax; t0 += 4) {
-                int nt = min(4, tmax - t0 + 1);
-                uint64_t bdesc = sdesc_sw64(bbase + (uint32_t)(t0 - 1) * TN * TK * 2 + kk * 32);
-                uint32_t col = (uint32_t)(s + t0 - 2) * TN;
-                uint32_t acc = (sic == 0 && kk == 0 && s == 1) ? 0u : 1u;
+              // descriptor start field = byte address / 16: offsets add to it directly
+              const uint64_t adesc = a0 + (uint64_t)((((s - 1) * TM * TK * 2) + kk * 32) >> 4);
+#pragma unroll
+              for (int t0 = 1; t0 <= MAXS; t0 += 4) {
+                if (t0 > tmax) break;
+                const int nt = min(4, tmax - t0 + 1);
+                const uint64_t bdesc = b0 + (uint64_t)((((t0 - 1) * TN * TK * 2) + kk * 32) >> 4);
+                const uint32_t col = (uint32_t)(s + t0 - 2) * TN;
+                const uint32_t acc = (sic == 0 && kk == 0 && s == 1) ? 0u : 1u;
                 umma(tmem + col, adesc, bdesc, idesc_bf16(nt * TN), acc);
               }
             }
@@ -424,6 +433,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__
       ok = mbar_wait(bar_accf, (uint32_t)c & 1u, p.st);
       if (!ok) break;
       tc_fence_after();
+#pragma unroll 1
       for (int lv = 0; lv < nlev; ++lv) {
         int l = lv + 2;
         float v[32];
@@ -539,7 +549,9 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
   if (KP < TK) return GEP_ERR_ALLOC;
   static int attr_done = 0;
   if (!attr_done) {
-    cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes_for(MAXS));
+    cudaFuncSetAttribute(k_oz_gemm<8, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes_for(MAXS));
+    cudaFuncSetAttribute(k_oz_gemm<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes_for(MAXS));
+    cudaFuncSetAttribute(k_oz_gemm<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes_for(MAXS));
     attr_done = 1;
   }
   int lower = (uplo == 'L' || uplo == 'l');
@@ -586,7 +598,9 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
         h->prof_skipped++;
       }
     }
-    k_oz_gemm<<<grid, NTHREADS, smem_bytes_for(S), h->stream>>>(mA, mB, a);
+    if (S == 8 && levels == 9) k_oz_gemm<8, 9><<<grid, NTHREADS, smem_bytes_for(S), h->stream>>>(mA, mB, a);
+    else if (S == 3 && levels == 4) k_oz_gemm<3, 4><<<grid, NTHREADS, smem_bytes_for(S), h->stream>>>(mA, mB, a);
+    else k_oz_gemm<0, 0><<<grid, NTHREADS, smem_bytes_for(S), h->stream>>>(mA, mB, a);
     GEP_CHECK(check_launch(h));
     if (slot >= 0) cudaEventRecord(h->prof_ev[2 * slot + 1], h->stream);
   }
