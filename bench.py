@@ -74,22 +74,24 @@ def run_compare_mixed(a):
     A = torch.as_tensor(tb["A"]).cuda()
     B = torch.as_tensor(tb["B"]).cuda()
     out = {"metric": "mixed+refined vs FP64-accurate GEP solve time", "M": M, "unit": "s",
-           "higher_is_better": False, "data": "synthetic", "config": {"workload": f"tight-binding GEP M={M}"}}
+           "higher_is_better": False, "data": "synthetic",
+           "config": {"workload": f"tight-binding GEP M={M}", "sep": a.sep}}
     res = {}
     for prec in ("fp64_emulated", "mixed_refined"):
         h = gep.Handle()
         for _ in range(max(1, a.warmup)):
-            w, Y, info = gep.solve(A, B, precision=prec, timers=True, handle=h)
+            w, Y, info = gep.solve(A, B, precision=prec, timers=True, handle=h, sep=a.sep)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(a.steps):
-            w, Y, info = gep.solve(A, B, precision=prec, timers=True, handle=h)
+            w, Y, info = gep.solve(A, B, precision=prec, timers=True, handle=h, sep=a.sep)
         e1.record()
         torch.cuda.synchronize()
         res[prec] = {"s": e0.elapsed_time(e1) / a.steps / 1e3, "info": info,
                      "stage_ms": [round(x, 1) for x in h.stage_times()],
-                     "check": sampled_check(A, B, w, Y, 64, a.seed)}
+                     "check": sampled_check(A, B, w, Y, 64, a.seed),
+                     "refine_steps": h.refine_steps() if prec == "mixed_refined" else 0}
         res[prec]["w"] = w.clone()
         h.close()
     nA = float(torch.linalg.eigvalsh(A).abs().max().item()) if M <= 8192 else float(A.abs().sum(1).max().item())

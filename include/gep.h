@@ -130,8 +130,8 @@ int sep_backtransform(gep_handle_t h, int M, int ncol, const double* C, int ldc,
  * Eigen_sx; "TRD/BAND" and "BACK" of Table 3) --------------------------------------
  * sep_q2_elems: number of doubles of the bulge-chasing reflector storage q2 for order M
  *   and bandwidth b (1 <= b <= 64; 0 for invalid arguments).
- * sep_tridiag_2stage: C = Q1 Q2 T Q2^T Q1^T in two stages.  Full -> band: C (lower on
- *   entry; both triangles are overwritten) becomes a matrix of bandwidth b, whose
+ * sep_tridiag_2stage: C = Q1 Q2 T Q2^T Q1^T in two stages.  Full -> band: C (lower
+ *   triangle read and overwritten, upper not referenced) becomes a matrix of bandwidth b, whose
  *   lower band (offsets 0..b) is kept, with the panel reflectors stored below the band
  *   (reflector j has its implied unit entry at row j+b) and their scalars in tau1[M]
  *   (tau1[j] = 0 where no reflector exists).  Band -> tridiagonal by bulge chasing:
@@ -238,11 +238,15 @@ long long gep_launch_count(gep_handle_t h, int reset);
 int gep_profile_enable(gep_handle_t h, int cap);
 int gep_profile_read(gep_handle_t h, double* ms, double* tensor_flops, double* fp64_flops, long long* launches,
                      long long* skipped, int reset);
+/* Recorded launch i (0 <= i < launches of gep_profile_read, before a reset): its product
+ * shape (m, n, k of that K panel) and CUDA-event time in ms.  Synchronises the stream. */
+int gep_profile_entry(gep_handle_t h, int i, int mnk[3], double* ms);
 
 const char* gep_status_string(int code);
 
 /* ---- FP64 matrix product (the dense contraction every stage is built on) ------
- * C = alpha op(A) op(B) + beta C, op = 'N' or 'T'; uplo 'F' (full) or 'L' (only
+ * C = alpha op(A) op(B) + beta C, op = 'N' or 'T'; transa 'S': A is symmetric (m x m,
+ * k = m, transb 'N') and only its lower triangle is read.  uplo 'F' (full) or 'L' (only
  * entries i >= j of C are computed and written).  engine: GEP_PREC_FP64 (FP64 FMA)
  * or GEP_PREC_FP64_EMULATED (split-BF16 tensor cores, FP64-accurate). */
 int gep_dgemm(gep_handle_t h, char transa, char transb, char uplo, int m, int n, int k, double alpha,

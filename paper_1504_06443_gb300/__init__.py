@@ -93,6 +93,7 @@ def load():
             "gep_get_stage_times": (_I, [_P, ctypes.POINTER(_D)]),
             "gep_launch_count": (ctypes.c_longlong, [_P, _I]),
             "gep_refine_steps": (_I, [_P]),
+            "gep_profile_entry": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
             "gep_get_band_times": (_I, [_P, ctypes.POINTER(_D)]),
             "gep_profile_enable": (_I, [_P, _I]),
             "gep_profile_read": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D),
@@ -201,6 +202,16 @@ class Handle:
 
     def launches(self, reset=False):
         return int(self.lib.gep_launch_count(self.h, 1 if reset else 0))
+
+    def profile_entries(self, count):
+        """[(m, n, k, ms)] of the first `count` recorded product launches."""
+        out = []
+        mnk = (_I * 3)()
+        ms = _D()
+        for i in range(int(count)):
+            _check(self.lib.gep_profile_entry(self.h, i, mnk, ctypes.byref(ms)), "gep_profile_entry")
+            out.append((mnk[0], mnk[1], mnk[2], ms.value))
+        return out
 
     def band_times(self):
         """(full->band ms, bulge-chasing ms) of the last two-stage solve with timers."""

@@ -211,6 +211,8 @@ int gep_profile_enable(gep_handle_t h, int cap) {
     delete[] h->prof_ev;
     delete[] h->prof_flops;
     delete[] h->prof_f64eq;
+    delete[] h->prof_mnk;
+    h->prof_mnk = nullptr;
     h->prof_ev = nullptr;
     h->prof_flops = h->prof_f64eq = nullptr;
   }
@@ -221,6 +223,7 @@ int gep_profile_enable(gep_handle_t h, int cap) {
   h->prof_ev = new cudaEvent_t[2 * (size_t)cap];
   h->prof_flops = new double[cap];
   h->prof_f64eq = new double[cap];
+  h->prof_mnk = new int[3 * (size_t)cap];
   for (int i = 0; i < 2 * cap; ++i) GEP_CUDA(cudaEventCreate(&h->prof_ev[i]));
   h->prof_cap = cap;
   h->prof_on = 1;
@@ -248,6 +251,18 @@ int gep_profile_read(gep_handle_t h, double* ms, double* tensor_flops, double* f
     h->prof_used = 0;
     h->prof_skipped = 0;
   }
+  return GEP_OK;
+}
+
+int gep_profile_entry(gep_handle_t h, int i, int mnk[3], double* ms) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (i < 0 || i >= h->prof_used) return -2;
+  if (!mnk || !ms) return -3;
+  GEP_CUDA(cudaStreamSynchronize(h->stream));
+  float e = 0.f;
+  GEP_CUDA(cudaEventElapsedTime(&e, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]));
+  for (int q = 0; q < 3; ++q) mnk[q] = h->prof_mnk[3 * i + q];
+  *ms = e;
   return GEP_OK;
 }
 
@@ -299,12 +314,14 @@ int gep_dgemm(gep_handle_t h, char transa, char transb, char uplo, int m, int n,
               int engine) {
   if (!handle_ok(h)) return GEP_ERR_HANDLE;
   bool ta = (transa == 'T' || transa == 't'), tb = (transb == 'T' || transb == 't');
-  if (!ta && transa != 'N' && transa != 'n') return -2;
+  bool sa = (transa == 'S' || transa == 's');
+  if (!ta && !sa && transa != 'N' && transa != 'n') return -2;
   if (!tb && transb != 'N' && transb != 'n') return -3;
+  if (sa && tb) return -3;
   if (uplo != 'F' && uplo != 'f' && uplo != 'L' && uplo != 'l') return -4;
   if (m < 0) return -5;
   if (n < 0) return -6;
-  if (k < 0) return -7;
+  if (k < 0 || (sa && k != m)) return -7;
   if (lda < (ta ? (k > 1 ? k : 1) : (m > 1 ? m : 1))) return -10;
   if (ldb < (tb ? (n > 1 ? n : 1) : (k > 1 ? k : 1))) return -12;
   if (ldc < (m > 1 ? m : 1)) return -15;

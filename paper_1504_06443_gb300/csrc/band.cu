@@ -6,8 +6,8 @@
 // reflectors (Q_p = I - V T V^T), R stays in the band and the trailing matrix takes
 // the two-sided update
 //     X = C22 V T,  W = X - V (T^T V^T X) / 2,  C22 <- C22 - W V^T - V W^T,
-// i.e. all O(M^3) work is matrix products (split-BF16 tensor-core engine).  C is kept
-// fully symmetric during this stage so that C22 V is a plain product.
+// i.e. all O(M^3) work is matrix products (split-BF16 tensor-core engine).  Only the
+// lower triangle of C22 is stored and updated; C22 V reads it as a symmetric operand.
 //
 // S1c band -> tridiagonal (bulge chasing).  Sweep s annihilates column s below the
 // subdiagonal with a reflector H(s,0) on rows s+1..s+b, then chases the bulge that
@@ -43,7 +43,7 @@ size_t rr(size_t n) { return (n + 31) & ~(size_t)31; }
 // ------------------------------------------------------------------ S1b panel QR
 
 // One Householder step (column c) of the QR factorisation of the n x nb panel P (ld ldp),
-// fused with the partial dot products the next step needs.  part_in[g][j] (g over the
+// fused with the partial dot products the next step needs.  part_in[j][g] (g over the
 // CTAs) = sum over rows r > c of P(r,c) P(r,j), prow_in[j] = P(c,j): the pivot row is
 // kept out of the sums so that the norm of the tail is never formed by cancellation.
 // c = -1 only produces part/prow for column 0.  The reflector follows LAPACK's dlarfg:
@@ -61,10 +61,14 @@ __global__ void __launch_bounds__(PQ_ROWS) k_pqr_step(int n, int nb, int c, doub
   const int r = blockIdx.x * PQ_ROWS + t;
   double tk = 0.0, scale = 0.0, beta = 0.0;
   if (c >= 0) {
-    if (t < nb && t >= c) {
-      double s = 0.0;
-      for (int g = 0; g < G; ++g) s += part_in[(size_t)g * BMAX + t];
-      sd[t] = s;
+    {  // column j's partials part_in[j * G + g]: one warp per column, fixed-order tree
+      const int w = t >> 5, lane = t & 31;
+      for (int j = c + w; j < nb; j += PQ_ROWS / 32) {
+        double s = 0.0;
+        for (int g = lane; g < G; g += 32) s += part_in[(size_t)j * G + g];
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) sd[j] = s;
+      }
     }
     __syncthreads();
     if (t == 0) {
@@ -130,7 +134,7 @@ __global__ void __launch_bounds__(PQ_ROWS) k_pqr_step(int n, int nb, int c, doub
     if (t < PQ_CH && cb + t < nb) {
       double s = 0.0;
       for (int sg = 0; sg < PQ_ROWS / PQ_CH; ++sg) s += seg[sg][t];
-      part_out[(size_t)blockIdx.x * BMAX + cb + t] = s;
+      part_out[(size_t)(cb + t) * G + blockIdx.x] = s;
     }
     __syncthreads();
   }
@@ -496,8 +500,9 @@ size_t band_ws_elems(int M, int b) {
   return reduce > chase ? reduce : chase;
 }
 
-// S1b.  C (M x M, lower on entry) -> band of width b in C (lower), reflectors below the
-// band, tau1[j] for columns j < M - b (zero where no reflector).
+// S1b.  C (M x M, lower triangle) -> band of width b in C (lower), reflectors below the
+// band, tau1[j] for columns j < M - b (zero where no reflector).  The upper triangle is
+// not referenced.
 int band_reduce(gep_handle_t h, int M, double* C, int ldc, int b, double* tau1, double* ws, size_t ws_elems,
                 int eng) {
   if (b < 1 || b > BMAX) return GEP_ERR_UNSUPPORTED;
@@ -505,7 +510,6 @@ int band_reduce(gep_handle_t h, int M, double* C, int ldc, int b, double* tau1, 
   if (M <= 0) return GEP_OK;
   GEP_CHECK(set_matrix(h, M, 1, 0.0, 0.0, tau1, M));
   if (M <= b + 1) return GEP_OK;
-  GEP_CHECK(symmetrize_lower(h, M, C, ldc));
   size_t Gmax = ((size_t)M + PQ_ROWS - 1) / PQ_ROWS;
   double* part0 = ws;
   double* part1 = part0 + rr(Gmax * BMAX);
@@ -539,15 +543,15 @@ int band_reduce(gep_handle_t h, int M, double* C, int ldc, int b, double* tau1, 
     GEP_CHECK(larft_rec(h, b, GV, b, tau1 + pb, T, b, Tt));
     double* C22 = C + (pb + b) + (size_t)(pb + b) * ldc;
     double* W = WVW;
-    GEP_CHECK(dgemm(h, 'N', 'N', 'F', n, b, n, 1.0, C22, ldc, V, n, 0.0, CV, n, eng));   // C22 V
+    GEP_CHECK(dgemm(h, 'S', 'N', 'F', n, b, n, 1.0, C22, ldc, V, n, 0.0, CV, n, eng));   // C22 V (lower stored)
     GEP_CHECK(dgemm(h, 'N', 'N', 'F', n, b, b, 1.0, CV, n, T, b, 0.0, W, n, eng));       // X = C22 V T
     GEP_CHECK(dgemm(h, 'T', 'N', 'F', b, b, n, 1.0, V, n, W, n, 0.0, Pm, b, eng));       // V^T X
     GEP_CHECK(dgemm(h, 'T', 'N', 'F', b, b, b, 1.0, T, b, Pm, b, 0.0, Ym, b, eng));      // T^T V^T X
     GEP_CHECK(dgemm(h, 'N', 'N', 'F', n, b, b, -0.5, V, n, Ym, b, 1.0, W, n, eng));      // W
     GEP_CHECK(copy_matrix(h, n, b, V, n, WVW + (size_t)n * b, n));
     GEP_CHECK(copy_matrix(h, n, b, W, n, WVW + (size_t)2 * n * b, n));
-    // C22 -= [W V] [V W]^T = W V^T + V W^T (both triangles: C stays symmetric)
-    GEP_CHECK(dgemm(h, 'N', 'T', 'F', n, n, 2 * b, -1.0, WVW, n, WVW + (size_t)n * b, n, 1.0, C22, ldc, eng));
+    // C22 -= [W V] [V W]^T = W V^T + V W^T (lower triangle)
+    GEP_CHECK(dgemm(h, 'N', 'T', 'L', n, n, 2 * b, -1.0, WVW, n, WVW + (size_t)n * b, n, 1.0, C22, ldc, eng));
   }
   return GEP_OK;
 }

@@ -1,4 +1,5 @@
-// FP64 FMA matrix product C = alpha op(A) op(B) + beta C (column-major).
+// FP64 FMA matrix product C = alpha op(A) op(B) + beta C (column-major); op(A) may also
+// be a symmetric matrix given by its lower triangle (transa 'S', m = k).
 //
 // The dense contraction under every blocked stage (trailing updates of the
 // Cholesky factorisation, triangular solves, the SYR2K update of the
@@ -15,7 +16,7 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16;
 
-template <bool TA, bool TB>
+template <bool TA, bool TB, bool SA = false>
 __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int k, double alpha,
                                                const double* __restrict__ A, int lda,
                                                const double* __restrict__ B, int ldb, double beta,
@@ -44,7 +45,10 @@ __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int k, double alpha
       else { kk = idx & 15; i = idx >> 4; }
       int gi = row0 + i, gk = k0 + kk;
       double v = 0.0;
-      if (gi < m && gk < k) v = TA ? A[GEP_IX(gk, gi, lda)] : A[GEP_IX(gi, gk, lda)];
+      if (gi < m && gk < k) {
+        if (SA) v = gi >= gk ? A[GEP_IX(gi, gk, lda)] : A[GEP_IX(gk, gi, lda)];  // symmetric, lower stored
+        else v = TA ? A[GEP_IX(gk, gi, lda)] : A[GEP_IX(gi, gk, lda)];
+      }
       As[kk][i] = v;
     }
 #pragma unroll
@@ -90,7 +94,7 @@ __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int k, double alpha
 
 // Split-K partial products for small outputs with long K: CTA (bi, bj, z) computes the
 // 64 x 64 tile over k in [z*kc, (z+1)*kc) into P[z] (m x n, leading dimension m).
-template <bool TA, bool TB>
+template <bool TA, bool TB, bool SA = false>
 __global__ void __launch_bounds__(256) k_dgemm_splitk(int m, int n, int k, int kc, const double* __restrict__ A,
                                                       int lda, const double* __restrict__ B, int ldb,
                                                       double* __restrict__ P, const int* __restrict__ st) {
@@ -115,7 +119,10 @@ __global__ void __launch_bounds__(256) k_dgemm_splitk(int m, int n, int k, int k
       else { kk = idx & 15; i = idx >> 4; }
       int gi = row0 + i, gk = k0 + kk;
       double v = 0.0;
-      if (gi < m && gk < ke) v = TA ? A[GEP_IX(gk, gi, lda)] : A[GEP_IX(gi, gk, lda)];
+      if (gi < m && gk < ke) {
+        if (SA) v = gi >= gk ? A[GEP_IX(gi, gk, lda)] : A[GEP_IX(gk, gi, lda)];
+        else v = TA ? A[GEP_IX(gk, gi, lda)] : A[GEP_IX(gi, gk, lda)];
+      }
       As[kk][i] = v;
     }
 #pragma unroll
@@ -192,6 +199,8 @@ int dgemm_f64(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, 
     return check_launch(h);
   }
   bool TA = (ta == 'T' || ta == 't'), TB = (tb == 'T' || tb == 't');
+  const bool SA = (ta == 'S' || ta == 's');  // A symmetric (m x m, k = m), lower triangle stored
+  if (SA && (TB || k != m)) return GEP_ERR_UNSUPPORTED;
   dim3 grid((m + BM - 1) / BM, (n + BN - 1) / BN);
   long long tiles = (long long)grid.x * grid.y;
   // A few output tiles with a long K leave most SMs idle: split K across CTAs.
@@ -206,7 +215,8 @@ int dgemm_f64(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, 
       int z = (k + kc - 1) / kc;
       dim3 g3(grid.x, grid.y, z);
       double* P = h->d_splitk;
-      if (!TA && !TB) k_dgemm_splitk<false, false><<<g3, 256, 0, h->stream>>>(m, n, k, kc, A, lda, B, ldb, P, h->d_status);
+      if (SA) k_dgemm_splitk<false, false, true><<<g3, 256, 0, h->stream>>>(m, n, k, kc, A, lda, B, ldb, P, h->d_status);
+      else if (!TA && !TB) k_dgemm_splitk<false, false><<<g3, 256, 0, h->stream>>>(m, n, k, kc, A, lda, B, ldb, P, h->d_status);
       else if (!TA && TB) k_dgemm_splitk<false, true><<<g3, 256, 0, h->stream>>>(m, n, k, kc, A, lda, B, ldb, P, h->d_status);
       else if (TA && !TB) k_dgemm_splitk<true, false><<<g3, 256, 0, h->stream>>>(m, n, k, kc, A, lda, B, ldb, P, h->d_status);
       else k_dgemm_splitk<true, true><<<g3, 256, 0, h->stream>>>(m, n, k, kc, A, lda, B, ldb, P, h->d_status);
@@ -216,7 +226,10 @@ int dgemm_f64(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, 
       return check_launch(h);
     }
   }
-  if (!TA && !TB)
+  if (SA)
+    k_dgemm<false, false, true><<<grid, 256, 0, h->stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, lower,
+                                                              h->d_status);
+  else if (!TA && !TB)
     k_dgemm<false, false><<<grid, 256, 0, h->stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, lower, h->d_status);
   else if (!TA && TB)
     k_dgemm<false, true><<<grid, 256, 0, h->stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, lower, h->d_status);

@@ -133,6 +133,92 @@ __global__ void __launch_bounds__(256) k_split(int R, int K, int Kpad, const dou
   }
 }
 
+// Symmetric operand given by its lower triangle (op(A) = A, A(i, kk) = C(max, min)), K
+// panel [kb, kb + kc): exponents in two passes (the part of row i left of the diagonal,
+// read down the rows; then the part of column i below it, read along the column), and
+// digit planes with the same arithmetic as k_split.
+__global__ void k_rowexp_sym_row(int R, int kb, int kc, const double* __restrict__ C, long long ldc,
+                                 int* __restrict__ raw, const int* st) {
+  // block (x: 256 rows, y: 64-deep slab of the panel); raw[r] must start at 0
+  if (status_bad(st)) return;
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  int k0 = kb + blockIdx.y * 64, kend = min(min(r, kb + kc - 1), k0 + 63);
+  int m = 0;
+  for (int kk = k0; kk <= kend; ++kk) m = max(m, exp_field(C[r + kk * ldc]));
+  if (m) atomicMax(raw + r, m);
+}
+
+__global__ void k_rowexp_sym_col(int R, int kb, int kc, const double* __restrict__ C, long long ldc,
+                                 int* __restrict__ e, const int* st) {
+  if (status_bad(st)) return;
+  int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (r >= R) return;
+  int m = 0;
+  for (int kk = max(r + 1, kb) + lane; kk < kb + kc; kk += 32) m = max(m, exp_field(C[kk + r * ldc]));
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) {
+    m = max(m, e[r]);
+    e[r] = m ? m - 1022 : 0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_split_sym(int R, int K, int Kpad, int kb, const double* __restrict__ C,
+                                                   long long ldc, const int* __restrict__ e, int S,
+                                                   unsigned short* __restrict__ out, const int* st) {
+  __shared__ double t[32][33];
+  if (status_bad(st)) return;
+  int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const bool kfast = r0 + 31 < kb + k0;  // tile strictly above the diagonal: read along columns of C
+  for (int q = ty; q < 32; q += 8) {
+    int r, kk;
+    if (kfast) { r = r0 + q; kk = k0 + tx; }
+    else { r = r0 + tx; kk = k0 + q; }
+    double v = 0.0;
+    if (r < R && kk < K) {
+      int g = kb + kk;
+      v = r >= g ? C[r + (long long)g * ldc] : C[g + (long long)r * ldc];
+    }
+    if (kfast) t[q][tx] = v; else t[tx][q] = v;
+  }
+  __syncthreads();
+  for (int q = ty; q < 32; q += 8) {
+    int r = r0 + q, kk = k0 + tx;
+    if (r >= R || kk >= Kpad) continue;
+    long long F = 0;
+    if (kk < K) {
+      long long bits = __double_as_longlong(t[q][tx]);
+      int E = (int)((bits >> 52) & 0x7FF);
+      if (E != 0) {
+        unsigned long long m = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        int sh = E - 1075 + 7 * S - e[r];
+        unsigned long long qv;
+        if (sh >= 0) {
+          qv = m << sh;
+        } else if (sh > -64) {
+          int rs = -sh;
+          qv = m >> rs;
+          unsigned long long rem = m & ((1ull << rs) - 1ull), half = 1ull << (rs - 1);
+          if (rem > half || (rem == half && (qv & 1ull))) ++qv;
+        } else {
+          qv = 0;
+        }
+        F = (bits < 0) ? -(long long)qv : (long long)qv;
+      }
+    }
+    size_t base = (size_t)r * Kpad + kk;
+    size_t plane = (size_t)R * Kpad;
+    for (int s = S - 1; s >= 1; --s) {
+      int d = (int)(F & 127);
+      if (d >= 64) d -= 128;
+      F = (F - d) >> 7;
+      out[base + (size_t)s * plane] = bf16_of_int(d);
+    }
+    out[base] = bf16_of_int((int)F);
+  }
+}
+
 // ------------------------------------------------------------------ PTX helpers
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -534,6 +620,8 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
   const int S = levels - 1;
   if (S < 1 || S > MAXS) return GEP_ERR_UNSUPPORTED;
   bool TA = (ta == 'T' || ta == 't'), TB = (tb == 'T' || tb == 't');
+  const bool SA = (ta == 'S' || ta == 's');  // A symmetric (m x m, k = m), lower triangle stored
+  if (SA && k != m) return GEP_ERR_UNSUPPORTED;
   // view of op(A) as rows i, depth kk: element at A[i*sra + kk*ska]
   long long sra = TA ? lda : 1, ska = TA ? 1 : lda;
   // view of op(B)^T as rows j, depth kk
@@ -567,13 +655,26 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
     int* eb = ea + m;
     const double* Ap = A + (size_t)kb * ska;
     const double* Bp = B + (size_t)kb * skb;
-    if (ska == 1) k_rowexp<<<(m * 32 + 255) / 256, 256, 0, h->stream>>>(m, kc, Ap, sra, ska, ea, h->d_status);
-    else k_rowexp<<<(m + 255) / 256, 256, 0, h->stream>>>(m, kc, Ap, sra, ska, ea, h->d_status);
+    if (SA) {
+      GEP_CUDA(cudaMemsetAsync(ea, 0, sizeof(int) * (size_t)m, h->stream));
+      k_rowexp_sym_row<<<dim3((m + 255) / 256, (kc + 63) / 64), 256, 0, h->stream>>>(m, kb, kc, A, lda, ea,
+                                                                                    h->d_status);
+      GEP_CHECK(check_launch(h));
+      k_rowexp_sym_col<<<(m * 32 + 255) / 256, 256, 0, h->stream>>>(m, kb, kc, A, lda, ea, h->d_status);
+    } else if (ska == 1) {
+      k_rowexp<<<(m * 32 + 255) / 256, 256, 0, h->stream>>>(m, kc, Ap, sra, ska, ea, h->d_status);
+    } else {
+      k_rowexp<<<(m + 255) / 256, 256, 0, h->stream>>>(m, kc, Ap, sra, ska, ea, h->d_status);
+    }
     GEP_CHECK(check_launch(h));
     if (skb == 1) k_rowexp<<<(n * 32 + 255) / 256, 256, 0, h->stream>>>(n, kc, Bp, srb, skb, eb, h->d_status);
     else k_rowexp<<<(n + 255) / 256, 256, 0, h->stream>>>(n, kc, Bp, srb, skb, eb, h->d_status);
     GEP_CHECK(check_launch(h));
-    k_split<<<dim3(kpad / 32, (m + 31) / 32), 256, 0, h->stream>>>(m, kc, kpad, Ap, sra, ska, ea, S, As, h->d_status);
+    if (SA)
+      k_split_sym<<<dim3(kpad / 32, (m + 31) / 32), 256, 0, h->stream>>>(m, kc, kpad, kb, A, lda, ea, S, As,
+                                                                         h->d_status);
+    else
+      k_split<<<dim3(kpad / 32, (m + 31) / 32), 256, 0, h->stream>>>(m, kc, kpad, Ap, sra, ska, ea, S, As, h->d_status);
     GEP_CHECK(check_launch(h));
     k_split<<<dim3(kpad / 32, (n + 31) / 32), 256, 0, h->stream>>>(n, kc, kpad, Bp, srb, skb, eb, S, Bs, h->d_status);
     GEP_CHECK(check_launch(h));
@@ -594,6 +695,9 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
         double f = 2.0 * m * n * (double)kc * (lower ? 0.5 : 1.0);
         h->prof_f64eq[slot] = f;
         h->prof_flops[slot] = f * npairs;
+        h->prof_mnk[3 * slot] = m;
+        h->prof_mnk[3 * slot + 1] = n;
+        h->prof_mnk[3 * slot + 2] = kc;
       } else {
         h->prof_skipped++;
       }

@@ -31,6 +31,7 @@ struct gep_handle_s {
   cudaEvent_t* prof_ev = nullptr;   // 2 * prof_cap events
   double* prof_flops = nullptr;     // tensor flops of each recorded launch
   double* prof_f64eq = nullptr;     // FP64-equivalent flops of each recorded launch
+  int* prof_mnk = nullptr;          // m, n, k of each recorded launch
   // batched solves: child handles, one per concurrent stream (created on first use)
   int nchild = 0;
   gep_handle_s* child[64] = {};

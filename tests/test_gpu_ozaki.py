@@ -87,3 +87,20 @@ def test_mixed_levels_are_fp32_grade(gep):
     out = host(gep.dgemm(dev(A), dev(B), engine="mixed_refined"))
     rel = np.max(np.abs(out - A @ B) / (np.abs(A) @ np.abs(B)))
     assert rel <= 2e-6, rel
+
+
+@pytest.mark.parametrize("engine", ["fp64", "fp64_emulated"])
+@pytest.mark.parametrize("m,n", [(130, 64), (300, 70), (5000, 64)])
+def test_symmetric_lower_operand(gep, engine, m, n):
+    """transa 'S': A symmetric, only its lower triangle read (the upper one holds NaN);
+    m = 5000 spans two K panels of the split-BF16 engine."""
+    rng = np.random.default_rng(m + n)
+    G = rng.standard_normal((m, m))
+    S = (G + G.T) / 2
+    A = np.tril(S) + np.triu(np.full((m, m), np.nan), 1)
+    B = rng.standard_normal((m, n))
+    ref = S @ B
+    out = host(gep.dgemm(dev(A), dev(B), "S", "N", engine=engine))
+    bound = 1e-14 * (np.abs(S) @ np.abs(B)) + 1e-300
+    assert np.all(np.isfinite(out))
+    assert np.all(np.abs(out - ref) <= bound * (4 if engine == "fp64" else 1) + 4 * m * 2.0 ** -52 * (np.abs(S) @ np.abs(B)) * (engine == "fp64"))
