@@ -38,7 +38,7 @@ def parse():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--precision", default="fp64_emulated", choices=["fp64_emulated", "fp64", "mixed_refined"])
     p.add_argument("--reducer", default="twosided", choices=["twosided", "explicit_inv"])
-    p.add_argument("--sep", default="1stage", choices=["1stage", "2stage"],
+    p.add_argument("--sep", default="2stage", choices=["1stage", "2stage"],
                    help="SEP reduction: 1-stage tridiagonalisation or full->band->tridiagonal")
     p.add_argument("--bandwidth", type=int, default=0, help="band width of --sep 2stage (0: library default 64)")
     p.add_argument("--values-only", action="store_true", help="eigenvalues only (T_evo of the paper's benchmark)")

@@ -425,7 +425,8 @@ __global__ void __launch_bounds__(256) k_q2_apply(int M, int b, int Q, int wt, c
 // lower group: every dependency keeps or lowers j and keeps or raises k, so tiles are
 // applied with J descending and K ascending, and inside a tile with j descending and k
 // ascending.  U(J, K) is the product of its diamonds in that order, built by applying
-// them to the identity, W x TB_COLS columns per CTA.
+// them to the identity, W x TB_COLS columns per CTA, and stored as U - I so that a tile
+// is applied as Z(rows) += (U - I) Z(rows).
 constexpr int TQ = 4;
 constexpr int TB_COLS = 32;  // tile columns per CTA in the build (8 lanes per column)
 
@@ -470,10 +471,10 @@ __global__ void __launch_bounds__(256) k_q2_tile_build(int M, int b, int Q, int 
     }
   }
   __syncthreads();
-  double* Ut = U + (size_t)K * W * W;  // W x W column-major
+  double* Ut = U + (size_t)K * W * W;  // U - I, W x W column-major
   for (int idx = t; idx < W * TB_COLS; idx += blockDim.x) {
     int r = idx % W, cc = idx / W;
-    if (c0 + cc < W) Ut[r + (size_t)(c0 + cc) * W] = Us[r * (TB_COLS + 1) + cc];
+    if (c0 + cc < W) Ut[r + (size_t)(c0 + cc) * W] = Us[r * (TB_COLS + 1) + cc] - (r == c0 + cc ? 1.0 : 0.0);
   }
 }
 
@@ -494,15 +495,58 @@ size_t q2_elems(int M, int b) {
 
 size_t band_ws_elems(int M, int b) {
   size_t G = ((size_t)M + PQ_ROWS - 1) / PQ_ROWS;
-  size_t reduce = 2 * rr(G * BMAX) + 2 * rr(BMAX) + 2 * rr((size_t)M * b) + rr((size_t)M * 3 * b) +
-                  5 * rr((size_t)b * b);
+  size_t reduce = 2 * rr(G * BMAX) + 2 * rr(BMAX) + 4 * rr((size_t)M * b) + rr((size_t)M * 3 * b) +
+                  2 * rr((size_t)M * 4 * b) + 6 * rr((size_t)2 * b * b);
   size_t chase = rr((size_t)2 * b * M) + rr((size_t)M);  // band + progress counters
   return reduce > chase ? reduce : chase;
 }
 
+namespace {
+
+struct BandWs {
+  double *part0, *part1, *prow0, *prow1;
+  double *V, *CV, *WVW, *V1, *W1, *AA, *BB;
+  double *GV, *T, *Tt, *Pm, *Ym, *Zs;
+};
+
+// QR of the n x b panel P (ld ldp): reflectors stay in P, tau[0..b), explicit V (n x b,
+// unit lower trapezoidal) and the compact-WY factor T (b x b).
+int panel_factor(gep_handle_t h, int n, int b, double* P, int ldp, double* tau, const BandWs& w, double* V,
+                 int eng) {
+  const int G = (n + PQ_ROWS - 1) / PQ_ROWS;
+  const int nref = n < b ? n : b;
+  double *pin = w.part0, *pout = w.part1, *rin = w.prow0, *rout = w.prow1;
+  k_pqr_step<<<G, PQ_ROWS, 0, h->stream>>>(n, b, -1, P, ldp, pin, rin, pout, rout, tau, h->d_status);
+  GEP_CHECK(check_launch(h));
+  for (int c = 0; c < nref; ++c) {
+    double* tp = pin; pin = pout; pout = tp;
+    tp = rin; rin = rout; rout = tp;
+    k_pqr_step<<<G, PQ_ROWS, 0, h->stream>>>(n, b, c, P, ldp, pin, rin, pout, rout, tau, h->d_status);
+    GEP_CHECK(check_launch(h));
+  }
+  k_panel_v<<<dim3((n + 255) / 256, b), 256, 0, h->stream>>>(n, b, P, ldp, V, h->d_status);
+  GEP_CHECK(check_launch(h));
+  GEP_CHECK(dgemm(h, 'T', 'N', 'F', b, b, n, 1.0, V, n, V, n, 0.0, w.GV, b, eng));
+  return larft_rec(h, b, w.GV, b, tau, w.T, b, w.Tt);
+}
+
+// W = X - V (T^T V^T X) / 2 with X = CV T (CV = C22 V, n x b): the two-sided update of
+// the trailing matrix is then C22 - W V^T - V W^T.
+int panel_w(gep_handle_t h, int n, int b, const double* V, const double* CV, double* W, const BandWs& w, int eng) {
+  GEP_CHECK(dgemm(h, 'N', 'N', 'F', n, b, b, 1.0, CV, n, w.T, b, 0.0, W, n, eng));    // X = C22 V T
+  GEP_CHECK(dgemm(h, 'T', 'N', 'F', b, b, n, 1.0, V, n, W, n, 0.0, w.Pm, b, eng));    // V^T X
+  GEP_CHECK(dgemm(h, 'T', 'N', 'F', b, b, b, 1.0, w.T, b, w.Pm, b, 0.0, w.Ym, b, eng));  // T^T V^T X
+  return dgemm(h, 'N', 'N', 'F', n, b, b, -0.5, V, n, w.Ym, b, 1.0, W, n, eng);
+}
+
+}  // namespace
+
 // S1b.  C (M x M, lower triangle) -> band of width b in C (lower), reflectors below the
 // band, tau1[j] for columns j < M - b (zero where no reflector).  The upper triangle is
-// not referenced.
+// not referenced.  Panels are taken in pairs (p, p+1): panel p+1's columns and diagonal
+// block first receive panel p's pending update, C22' V1 is formed from the not yet
+// updated matrix minus the two low-rank corrections W (V^T V1) + V (W^T V1), and both
+// updates are applied together as one rank-4b product of depth 4b.
 int band_reduce(gep_handle_t h, int M, double* C, int ldc, int b, double* tau1, double* ws, size_t ws_elems,
                 int eng) {
   if (b < 1 || b > BMAX) return GEP_ERR_UNSUPPORTED;
@@ -511,47 +555,65 @@ int band_reduce(gep_handle_t h, int M, double* C, int ldc, int b, double* tau1, 
   GEP_CHECK(set_matrix(h, M, 1, 0.0, 0.0, tau1, M));
   if (M <= b + 1) return GEP_OK;
   size_t Gmax = ((size_t)M + PQ_ROWS - 1) / PQ_ROWS;
-  double* part0 = ws;
-  double* part1 = part0 + rr(Gmax * BMAX);
-  double* prow0 = part1 + rr(Gmax * BMAX);
-  double* prow1 = prow0 + rr(BMAX);
-  double* V = prow1 + rr(BMAX);
-  double* CV = V + rr((size_t)M * b);
-  double* WVW = CV + rr((size_t)M * b);
-  double* GV = WVW + rr((size_t)M * 3 * b);
-  double* T = GV + rr((size_t)b * b);
-  double* Tt = T + rr((size_t)b * b);
-  double* Pm = Tt + rr((size_t)b * b);
-  double* Ym = Pm + rr((size_t)b * b);
-  for (int pb = 0; M - pb - b >= 2; pb += b) {
+  BandWs w;
+  double* q = ws;
+  auto take = [&](size_t n) { double* p = q; q += rr(n); return p; };
+  w.part0 = take(Gmax * BMAX);
+  w.part1 = take(Gmax * BMAX);
+  w.prow0 = take(BMAX);
+  w.prow1 = take(BMAX);
+  w.V = take((size_t)M * b);
+  w.CV = take((size_t)M * b);
+  w.V1 = take((size_t)M * b);
+  w.W1 = take((size_t)M * b);
+  w.WVW = take((size_t)M * 3 * b);
+  w.AA = take((size_t)M * 4 * b);
+  w.BB = take((size_t)M * 4 * b);
+  w.GV = take((size_t)2 * b * b);
+  w.T = take((size_t)2 * b * b);
+  w.Tt = take((size_t)2 * b * b);
+  w.Pm = take((size_t)2 * b * b);
+  w.Ym = take((size_t)2 * b * b);
+  w.Zs = take((size_t)2 * b * b);
+  for (int pb = 0; M - pb - b >= 2;) {
     const int n = M - pb - b;
     double* P = C + (pb + b) + (size_t)pb * ldc;
-    const int G = (n + PQ_ROWS - 1) / PQ_ROWS;
-    const int nref = n < b ? n : b;
-    double *pin = part0, *pout = part1, *rin = prow0, *rout = prow1;
-    k_pqr_step<<<G, PQ_ROWS, 0, h->stream>>>(n, b, -1, P, ldc, pin, rin, pout, rout, tau1 + pb, h->d_status);
-    GEP_CHECK(check_launch(h));
-    for (int c = 0; c < nref; ++c) {
-      double* tp = pin; pin = pout; pout = tp;
-      tp = rin; rin = rout; rout = tp;
-      k_pqr_step<<<G, PQ_ROWS, 0, h->stream>>>(n, b, c, P, ldc, pin, rin, pout, rout, tau1 + pb, h->d_status);
-      GEP_CHECK(check_launch(h));
-    }
-    k_panel_v<<<dim3((n + 255) / 256, b), 256, 0, h->stream>>>(n, b, P, ldc, V, h->d_status);
-    GEP_CHECK(check_launch(h));
-    GEP_CHECK(dgemm(h, 'T', 'N', 'F', b, b, n, 1.0, V, n, V, n, 0.0, GV, b, eng));
-    GEP_CHECK(larft_rec(h, b, GV, b, tau1 + pb, T, b, Tt));
     double* C22 = C + (pb + b) + (size_t)(pb + b) * ldc;
-    double* W = WVW;
-    GEP_CHECK(dgemm(h, 'S', 'N', 'F', n, b, n, 1.0, C22, ldc, V, n, 0.0, CV, n, eng));   // C22 V (lower stored)
-    GEP_CHECK(dgemm(h, 'N', 'N', 'F', n, b, b, 1.0, CV, n, T, b, 0.0, W, n, eng));       // X = C22 V T
-    GEP_CHECK(dgemm(h, 'T', 'N', 'F', b, b, n, 1.0, V, n, W, n, 0.0, Pm, b, eng));       // V^T X
-    GEP_CHECK(dgemm(h, 'T', 'N', 'F', b, b, b, 1.0, T, b, Pm, b, 0.0, Ym, b, eng));      // T^T V^T X
-    GEP_CHECK(dgemm(h, 'N', 'N', 'F', n, b, b, -0.5, V, n, Ym, b, 1.0, W, n, eng));      // W
-    GEP_CHECK(copy_matrix(h, n, b, V, n, WVW + (size_t)n * b, n));
-    GEP_CHECK(copy_matrix(h, n, b, W, n, WVW + (size_t)2 * n * b, n));
-    // C22 -= [W V] [V W]^T = W V^T + V W^T (lower triangle)
-    GEP_CHECK(dgemm(h, 'N', 'T', 'L', n, n, 2 * b, -1.0, WVW, n, WVW + (size_t)n * b, n, 1.0, C22, ldc, eng));
+    double* W = w.WVW;  // [W | V | W]
+    GEP_CHECK(panel_factor(h, n, b, P, ldc, tau1 + pb, w, w.V, eng));
+    GEP_CHECK(dgemm(h, 'S', 'N', 'F', n, b, n, 1.0, C22, ldc, w.V, n, 0.0, w.CV, n, eng));  // C22 V
+    GEP_CHECK(panel_w(h, n, b, w.V, w.CV, W, w, eng));
+    GEP_CHECK(copy_matrix(h, n, b, w.V, n, w.WVW + (size_t)n * b, n));
+    GEP_CHECK(copy_matrix(h, n, b, W, n, w.WVW + (size_t)2 * n * b, n));
+    const int n1 = n - b;  // trailing order after panel p+1
+    if (n1 < 2) {
+      // C22 -= [W V] [V W]^T (lower triangle)
+      GEP_CHECK(dgemm(h, 'N', 'T', 'L', n, n, 2 * b, -1.0, w.WVW, n, w.WVW + (size_t)n * b, n, 1.0, C22, ldc, eng));
+      pb += b;
+      continue;
+    }
+    // panel p+1 = C22(b:, 0:b), its diagonal block C22(0:b, 0:b): apply panel p's update
+    double* P1 = C22 + b;
+    GEP_CHECK(dgemm(h, 'N', 'T', 'L', b, b, 2 * b, -1.0, w.WVW, n, w.WVW + (size_t)n * b, n, 1.0, C22, ldc, eng));
+    GEP_CHECK(dgemm(h, 'N', 'T', 'F', n1, b, 2 * b, -1.0, w.WVW + b, n, w.WVW + (size_t)n * b, n, 1.0, P1, ldc,
+                    eng));
+    GEP_CHECK(panel_factor(h, n1, b, P1, ldc, tau1 + pb + b, w, w.V1, eng));
+    double* C22b = C22 + b + (size_t)b * ldc;  // not yet updated by panel p
+    GEP_CHECK(dgemm(h, 'S', 'N', 'F', n1, b, n1, 1.0, C22b, ldc, w.V1, n1, 0.0, w.CV, n1, eng));
+    // Zs = [V' W']^T V1 (2b x b), CV -= [W' V'] Zs  (' = rows b.. of panel p's V, W)
+    GEP_CHECK(dgemm(h, 'T', 'N', 'F', 2 * b, b, n1, 1.0, w.WVW + (size_t)n * b + b, n, w.V1, n1, 0.0, w.Zs, 2 * b,
+                    eng));
+    GEP_CHECK(dgemm(h, 'N', 'N', 'F', n1, b, 2 * b, -1.0, w.WVW + b, n, w.Zs, 2 * b, 1.0, w.CV, n1, eng));
+    GEP_CHECK(panel_w(h, n1, b, w.V1, w.CV, w.W1, w, eng));
+    // C22b -= [W' V' W1 V1] [V' W' V1 W1]^T (lower triangle, depth 4b)
+    GEP_CHECK(copy_matrix(h, n1, 2 * b, w.WVW + b, n, w.AA, n1));                     // W' V'
+    GEP_CHECK(copy_matrix(h, n1, b, w.W1, n1, w.AA + (size_t)2 * b * n1, n1));      // W1
+    GEP_CHECK(copy_matrix(h, n1, b, w.V1, n1, w.AA + (size_t)3 * b * n1, n1));      // V1
+    GEP_CHECK(copy_matrix(h, n1, 2 * b, w.WVW + (size_t)n * b + b, n, w.BB, n1));    // V' W'
+    GEP_CHECK(copy_matrix(h, n1, b, w.V1, n1, w.BB + (size_t)2 * b * n1, n1));      // V1
+    GEP_CHECK(copy_matrix(h, n1, b, w.W1, n1, w.BB + (size_t)3 * b * n1, n1));      // W1
+    GEP_CHECK(dgemm(h, 'N', 'T', 'L', n1, n1, 4 * b, -1.0, w.AA, n1, w.BB, n1, 1.0, C22b, ldc, eng));
+    pb += 2 * b;
   }
   return GEP_OK;
 }
@@ -630,8 +692,15 @@ int apply_q2(gep_handle_t h, int M, int b, const double* q2, double* Z, int ldz,
         if (r0 >= M) break;
         const int Wc = (M - r0) < W ? (M - r0) : W;
         const double* Ut = U + (size_t)K * W * W;
-        GEP_CHECK(dgemm(h, 'N', 'N', 'F', Wc, ncol, Wc, 1.0, Ut, W, Z + r0, ldz, 0.0, Tmp, Wc, engine));
-        GEP_CHECK(copy_matrix(h, Wc, ncol, Tmp, Wc, Z + r0, ldz));
+        // one K panel of the split-BF16 engine: all of Z(rows) is split into digit planes
+        // before its product kernel writes C, so the update may run in place
+        const size_t one_panel = (size_t)16 * (Wc + ncol) * ((Wc + 31) / 32 * 32) + (size_t)4 * (Wc + ncol) + 4096;
+        if (Wc >= 128 && ncol >= 64 && Wc <= 4096 && one_panel <= h->eng_bytes) {
+          GEP_CHECK(dgemm(h, 'N', 'N', 'F', Wc, ncol, Wc, 1.0, Ut, W, Z + r0, ldz, 1.0, Z + r0, ldz, engine));
+        } else {  // Z(rows) += (U - I) copy(Z(rows))
+          GEP_CHECK(copy_matrix(h, Wc, ncol, Z + r0, ldz, Tmp, Wc));
+          GEP_CHECK(dgemm(h, 'N', 'N', 'F', Wc, ncol, Wc, 1.0, Ut, W, Tmp, Wc, 1.0, Z + r0, ldz, engine));
+        }
       }
     }
     return GEP_OK;

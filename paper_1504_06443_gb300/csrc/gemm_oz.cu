@@ -77,6 +77,54 @@ __device__ __forceinline__ unsigned short bf16_of_int(int d) {
   return (unsigned short)(((d < 0) ? 0x8000u : 0u) | ((unsigned)(127 + p) << 7) | mant);
 }
 
+// F = round(x 2^(7S - e)) as a signed integer (|F| < 2^(7S)), from the IEEE bits.
+__device__ __forceinline__ long long to_fixed(double x, int e, int S) {
+  long long bits = __double_as_longlong(x);
+  int E = (int)((bits >> 52) & 0x7FF);
+  if (E == 0) return 0;
+  unsigned long long m = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  int sh = E - 1075 + 7 * S - e;
+  unsigned long long qv;
+  if (sh >= 0) {
+    qv = m << sh;
+  } else if (sh > -64) {
+    int rs = -sh;
+    qv = m >> rs;
+    unsigned long long rem = m & ((1ull << rs) - 1ull), half = 1ull << (rs - 1);
+    if (rem > half || (rem == half && (qv & 1ull))) ++qv;
+  } else {
+    qv = 0;
+  }
+  return (bits < 0) ? -(long long)qv : (long long)qv;
+}
+
+// Digits of 4 consecutive elements x[0..3] of row r (columns kk .. kk+3, all < Kpad;
+// columns >= K are zero) written as one 8-byte store per plane.
+__device__ __forceinline__ void split4_store(const double* x, int kk, int K, int e, int S, size_t base,
+                                             size_t plane, unsigned short* __restrict__ out) {
+  long long F[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) F[u] = (kk + u < K) ? to_fixed(x[u], e, S) : 0ll;
+  for (int s = S - 1; s >= 1; --s) {
+    unsigned short b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int d = (int)(F[u] & 127);
+      if (d >= 64) d -= 128;
+      F[u] = (F[u] - d) >> 7;
+      b[u] = bf16_of_int(d);
+    }
+    uint2 w;
+    w.x = (unsigned)b[0] | ((unsigned)b[1] << 16);
+    w.y = (unsigned)b[2] | ((unsigned)b[3] << 16);
+    *reinterpret_cast<uint2*>(out + base + (size_t)s * plane) = w;
+  }
+  uint2 w;
+  w.x = (unsigned)bf16_of_int((int)F[0]) | ((unsigned)bf16_of_int((int)F[1]) << 16);
+  w.y = (unsigned)bf16_of_int((int)F[2]) | ((unsigned)bf16_of_int((int)F[3]) << 16);
+  *reinterpret_cast<uint2*>(out + base) = w;
+}
+
 // Digit planes out[s][r][kk] (bf16, kk contiguous, Kpad columns, zero padding).
 // x 2^-e[r] is rounded to the integer F = round(x 2^(7S-e)) (|F| < 2^(7S)), whose
 // balanced base-128 digits are peeled off from the least significant end:
@@ -97,39 +145,13 @@ __global__ void __launch_bounds__(256) k_split(int R, int K, int Kpad, const dou
     if (sk == 1) t[q][tx] = v; else t[tx][q] = v;
   }
   __syncthreads();
-  for (int q = ty; q < 32; q += 8) {
-    int r = r0 + q, kk = k0 + tx;
-    if (r >= R || kk >= Kpad) continue;
-    long long F = 0;
-    if (kk < K) {
-      long long bits = __double_as_longlong(t[q][tx]);
-      int E = (int)((bits >> 52) & 0x7FF);
-      if (E != 0) {
-        unsigned long long m = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        int sh = E - 1075 + 7 * S - e[r];
-        unsigned long long qv;
-        if (sh >= 0) {
-          qv = m << sh;
-        } else if (sh > -64) {
-          int rs = -sh;
-          qv = m >> rs;
-          unsigned long long rem = m & ((1ull << rs) - 1ull), half = 1ull << (rs - 1);
-          if (rem > half || (rem == half && (qv & 1ull))) ++qv;
-        } else {
-          qv = 0;
-        }
-        F = (bits < 0) ? -(long long)qv : (long long)qv;
-      }
+  {  // thread: row r0 + (tid >> 3), columns k0 + 4 (tid & 7) .. + 3
+    const int q = threadIdx.x >> 3, c4 = (threadIdx.x & 7) * 4;
+    const int r = r0 + q;
+    if (r < R) {
+      double x[4] = {t[q][c4], t[q][c4 + 1], t[q][c4 + 2], t[q][c4 + 3]};
+      split4_store(x, k0 + c4, K, e[r], S, (size_t)r * Kpad + k0 + c4, (size_t)R * Kpad, out);
     }
-    size_t base = (size_t)r * Kpad + kk;
-    size_t plane = (size_t)R * Kpad;
-    for (int s = S - 1; s >= 1; --s) {
-      int d = (int)(F & 127);
-      if (d >= 64) d -= 128;
-      F = (F - d) >> 7;
-      out[base + (size_t)s * plane] = bf16_of_int(d);
-    }
-    out[base] = bf16_of_int((int)F);
   }
 }
 
@@ -183,39 +205,13 @@ __global__ void __launch_bounds__(256) k_split_sym(int R, int K, int Kpad, int k
     if (kfast) t[q][tx] = v; else t[tx][q] = v;
   }
   __syncthreads();
-  for (int q = ty; q < 32; q += 8) {
-    int r = r0 + q, kk = k0 + tx;
-    if (r >= R || kk >= Kpad) continue;
-    long long F = 0;
-    if (kk < K) {
-      long long bits = __double_as_longlong(t[q][tx]);
-      int E = (int)((bits >> 52) & 0x7FF);
-      if (E != 0) {
-        unsigned long long m = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        int sh = E - 1075 + 7 * S - e[r];
-        unsigned long long qv;
-        if (sh >= 0) {
-          qv = m << sh;
-        } else if (sh > -64) {
-          int rs = -sh;
-          qv = m >> rs;
-          unsigned long long rem = m & ((1ull << rs) - 1ull), half = 1ull << (rs - 1);
-          if (rem > half || (rem == half && (qv & 1ull))) ++qv;
-        } else {
-          qv = 0;
-        }
-        F = (bits < 0) ? -(long long)qv : (long long)qv;
-      }
+  {
+    const int q = threadIdx.x >> 3, c4 = (threadIdx.x & 7) * 4;
+    const int r = r0 + q;
+    if (r < R) {
+      double x[4] = {t[q][c4], t[q][c4 + 1], t[q][c4 + 2], t[q][c4 + 3]};
+      split4_store(x, k0 + c4, K, e[r], S, (size_t)r * Kpad + k0 + c4, (size_t)R * Kpad, out);
     }
-    size_t base = (size_t)r * Kpad + kk;
-    size_t plane = (size_t)R * Kpad;
-    for (int s = S - 1; s >= 1; --s) {
-      int d = (int)(F & 127);
-      if (d >= 64) d -= 128;
-      F = (F - d) >> 7;
-      out[base + (size_t)s * plane] = bf16_of_int(d);
-    }
-    out[base] = bf16_of_int((int)F);
   }
 }
 
@@ -386,6 +382,7 @@ __device__ __forceinline__ double fixed_to_double(long long hi, long long lo, in
 
 struct OzArgs {
   int m, n, kpad, S, lmax, lower;
+  int gx, ntiles;  // tile grid: tile t covers rows 128 (t % gx) .., columns 64 (t / gx) ..
   const int* ea;
   const int* eb;
   double alpha, beta;
@@ -404,9 +401,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__
   __shared__ __align__(8) unsigned long long bars[2 * STAGES + 3];
   __shared__ uint32_t tmem_slot;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tm = blockIdx.x * TM, tn = blockIdx.y * TN;
   __shared__ int skip;
-  if (p.lower && tm + TM - 1 < tn) return;  // tile strictly above the diagonal (uniform)
+  // persistent: CTA b takes tiles b, b + gridDim.x, ...; tiles strictly above the
+  // diagonal of a lower-triangle product are skipped by every role alike
+  auto tile_rc = [&](int t, int& tm, int& tn) {
+    tm = (t % p.gx) * TM;
+    tn = (t / p.gx) * TN;
+    return !(p.lower && tm + TM - 1 < tn);
+  };
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int S = SC > 0 ? SC : p.S, LMAX = LC > 0 ? LC : p.lmax;
   const uint32_t a_bytes = (uint32_t)S * TM * TK * 2, b_bytes = (uint32_t)S * TN * TK * 2;
@@ -446,35 +448,42 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__
 
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;
+      int g = 0;  // k-steps issued by this CTA over all its tiles
       bool ok = true;
-      for (int step = 0; step < nsteps && ok; ++step) {
-        int sidx = step % STAGES;
-        uint32_t ph = (uint32_t)(step / STAGES) & 1u;
-        ok = mbar_wait(bar_empty + 8 * sidx, ph ^ 1u, p.st);
-        if (!ok) break;
-        uint32_t dst = smem_u32(smem + (size_t)sidx * stage_bytes);
-        mbar_expect_tx(bar_full + 8 * sidx, stage_bytes);
-        tma_load_3d(dst, &tmA, step * TK, tm, 0, bar_full + 8 * sidx);
-        tma_load_3d(dst + a_bytes, &tmB, step * TK, tn, 0, bar_full + 8 * sidx);
-        issued = step + 1;
+      for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+        int tm, tn;
+        if (!tile_rc(t, tm, tn)) continue;
+        for (int step = 0; step < nsteps && ok; ++step, ++g) {
+          int sidx = g % STAGES;
+          uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          ok = mbar_wait(bar_empty + 8 * sidx, ph ^ 1u, p.st);
+          if (!ok) break;
+          uint32_t dst = smem_u32(smem + (size_t)sidx * stage_bytes);
+          mbar_expect_tx(bar_full + 8 * sidx, stage_bytes);
+          tma_load_3d(dst, &tmA, step * TK, tm, 0, bar_full + 8 * sidx);
+          tma_load_3d(dst + a_bytes, &tmB, step * TK, tn, 0, bar_full + 8 * sidx);
+        }
       }
       // make sure every copy this thread started has landed before the CTA retires
-      for (int step = (issued > STAGES ? issued - STAGES : 0); step < issued; ++step)
-        mbar_wait(bar_full + 8 * (step % STAGES), (uint32_t)(step / STAGES) & 1u, p.st);
+      for (int s2 = (g > STAGES ? g - STAGES : 0); s2 < g; ++s2)
+        mbar_wait(bar_full + 8 * (s2 % STAGES), (uint32_t)(s2 / STAGES) & 1u, p.st);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       bool ok = true;
+      int g = 0, gc = 0;  // k-steps and chunks consumed over all tiles
+      for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+      int tm, tn;
+      if (!tile_rc(t, tm, tn)) continue;
       int step = 0;
-      for (int c = 0; c < nchunks && ok; ++c) {
-        ok = mbar_wait(bar_acce, ((uint32_t)c & 1u) ^ 1u, p.st);
+      for (int c = 0; c < nchunks && ok; ++c, ++gc) {
+        ok = mbar_wait(bar_acce, ((uint32_t)gc & 1u) ^ 1u, p.st);
         if (!ok) break;
         tc_fence_after();
         int send = min(nsteps, (c + 1) * (KCH / TK));
-        for (int sic = 0; step < send; ++step, ++sic) {
-          int sidx = step % STAGES;
-          ok = mbar_wait(bar_full + 8 * sidx, (uint32_t)(step / STAGES) & 1u, p.st);
+        for (int sic = 0; step < send; ++step, ++sic, ++g) {
+          int sidx = g % STAGES;
+          ok = mbar_wait(bar_full + 8 * sidx, (uint32_t)(g / STAGES) & 1u, p.st);
           if (!ok) break;
           tc_fence_after();
           uint32_t abase = smem_u32(smem + (size_t)sidx * stage_bytes);
@@ -504,19 +513,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__
         if (!ok) break;
         umma_commit(bar_accf);
       }
+      }
       umma_commit(bar_done);
       mbar_wait(bar_done, 0, p.st);
     }
   } else {
     // epilogue: warp w reads TMEM lanes 32*(w%4).., columns 32*((w-2)/4)..
     const int q = warp & 3, half = (warp - 2) >> 2;
+    bool ok = true;
+    int gc = 0;
+    for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+    int tm, tn;
+    if (!tile_rc(t, tm, tn)) continue;
     const int row = tm + q * 32 + lane;
     long long hi[32], lo[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) { hi[j] = 0; lo[j] = 0; }
-    bool ok = true;
-    for (int c = 0; c < nchunks; ++c) {
-      ok = mbar_wait(bar_accf, (uint32_t)c & 1u, p.st);
+    for (int c = 0; c < nchunks; ++c, ++gc) {
+      ok = mbar_wait(bar_accf, (uint32_t)gc & 1u, p.st);
       if (!ok) break;
       tc_fence_after();
 #pragma unroll 1
@@ -554,6 +568,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__
         if (beta != 0.0) out = fma(beta, *cp, out);
         *cp = out;
       }
+    }
     }
   }
   tc_fence_before();
@@ -684,7 +699,10 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
     OzArgs a;
     a.m = m; a.n = n; a.kpad = kpad; a.S = S; a.lmax = levels; a.lower = lower;
     a.ea = ea; a.eb = eb; a.alpha = alpha; a.beta = (kb == 0) ? beta : 1.0; a.C = C; a.ldc = ldc; a.st = h->d_status;
-    dim3 grid((m + TM - 1) / TM, (n + TN - 1) / TN);
+    const int gx = (m + TM - 1) / TM, gy = (n + TN - 1) / TN;
+    a.gx = gx;
+    a.ntiles = gx * gy;
+    dim3 grid(a.ntiles < h->sm_count ? a.ntiles : h->sm_count);  // persistent CTAs
     int slot = -1;
     if (h->prof_on) {
       if (h->prof_used < h->prof_cap) {
