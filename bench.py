@@ -111,12 +111,21 @@ def run_batched(a):
     import gep_inputs as gi
     from paper_1504_06443_gb300 import build as gbuild
     import paper_1504_06443_gb300 as gep
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    dist = None
+    if world > 1:  # independent pencils: LPT shares, no exchange on the data path
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl", device_id=torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0"))))
     gbuild.build()
-    orders = gi.batch_orders(a.batch_count, seed=1000)
+    all_orders = gi.batch_orders(a.batch_count, seed=1000)
+    mine = gep.shard_batch(all_orders, world)[rank]
+    orders = [all_orders[i] for i in mine]
     t0 = time.time()
     As, Bs = [], []
-    for i, M in enumerate(orders):
-        tb = gi.tight_binding(M, 1000 + i)
+    for i, M in zip(mine, orders):
+        tb = gi.tight_binding(M, 1000 + i)  # pencil i of the whole batch, whichever rank solves it
         As.append(torch.as_tensor(tb["A"]).cuda())
         Bs.append(torch.as_tensor(tb["B"]).cuda())
     gen_s = time.time() - t0
@@ -139,22 +148,41 @@ def run_batched(a):
     for _ in range(a.warmup):
         bs.replay()
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
     e0.record()
     for _ in range(a.steps):
         bs.replay()
     e1.record()
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     s = e0.elapsed_time(e1) / a.steps / 1e3
     info = bs.info()
+    if dist:
+        t = torch.tensor([s, loop_s, float(info)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        s, loop_s, info = t[0].item(), t[1].item(), int(t[2].item())
+        flops = sum(7.0 * float(M) ** 3 for M in all_orders)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    orders = all_orders
     out = {"metric": "batched GEP throughput (all eigenpairs)", "value": len(orders) / s, "unit": "GEPs/s",
+           "n_gpus": world, "scaling": "strong" if world > 1 else None,
            "higher_is_better": True, "seconds_per_batch": s, "looping_single_solves_s": loop_s,
            "speedup_vs_loop": loop_s / s, "fp64_equiv_tflops": flops / s / 1e12, "info": info,
            "steps": a.steps, "warmup": a.warmup, "data": "synthetic", "dtype": "f64",
            "config": {"workload": f"{len(orders)} tight-binding pencils, M log-uniform in [64, 2048]",
                       "orders_min_max": [min(orders), max(orders)], "nstreams": 16, "graph": "one captured CUDA graph",
                       "autotuned_engine_per_bucket": {str(k): v for k, v in choice.items()},
-                      "generator_s": round(gen_s, 1)}}
+                      "generator_s": round(gen_s, 1),
+                      "parallelism": f"LPT shards of the batch over {world} ranks" if world > 1 else "single"}}
     print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
 
 def run_adjoint(a):

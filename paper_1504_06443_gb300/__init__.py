@@ -20,7 +20,7 @@ import threading
 __all__ = ["load", "solve", "solve_host", "cholesky", "reduce", "tridiag_1stage", "tridiag_eig",
            "sep_backtransform", "tridiag_2stage", "sep_backtransform_2stage", "gep_backtransform", "dgemm", "Handle", "default_handle",
            "RED_TWOSIDED", "RED_EXPLICIT_INV", "SEP_1STAGE", "SEP_2STAGE", "PREC_FP64",
-           "PREC_FP64_EMULATED", "PREC_MIXED_REFINED", "GepError"]
+           "PREC_FP64_EMULATED", "PREC_MIXED_REFINED", "GepError", "shard_batch"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libgep.so")
@@ -535,6 +535,22 @@ def eigh_density(A, B, n_occ, precision="fp64_emulated"):
 # ------------------------------------------------------------------ batched
 
 SIZE_BUCKETS = (128, 256, 512, 1024, 2048, 4096)
+
+
+def shard_batch(orders, world):
+    """Longest-processing-time partition of independent pencils over `world` ranks:
+    pencils in decreasing M^3 (ties: lower index first), each to the rank with the least
+    assigned M^3 so far (ties: lower rank).  Returns one ascending index list per rank.
+    The batched form needs no exchange between ranks: each solves its own pencils."""
+    world = max(1, int(world))
+    order = sorted(range(len(orders)), key=lambda i: (-float(orders[i]) ** 3, i))
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += float(orders[i]) ** 3
+    return [sorted(p) for p in parts]
 
 
 def _bucket(M):

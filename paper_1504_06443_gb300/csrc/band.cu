@@ -448,14 +448,20 @@ __global__ void __launch_bounds__(256) k_q2_tile_build(int M, int b, int Q, int 
   __syncthreads();
   const int col = t >> 3, part = t & 7;
   const int jhi = min(J0 + TQ - 1, Q);
+  // rows [rmin, rmax] hold every nonzero of this CTA's columns (identity columns at
+  // first): a reflector whose rows miss that range leaves them unchanged and is skipped
+  int rmin = c0, rmax = c0 + TB_COLS - 1;
   for (int j = jhi; j >= J0; --j) {
     for (int k = K0; k < K0 + TQ; ++k) {
       if (k > Q - j) continue;
       const double* D0 = q2 + diamond_index(Q, j, k) * diamond_elems(b);
       const int lo = (j + k - J0 - K0) * b;  // tile row of the diamond's row 0
       for (int c = b - 1; c >= 0; --c) {
+        if (lo + c + b - 1 < rmin || lo + c > rmax) continue;
         double tc = D0[(size_t)2 * b * b + c];
         if (tc == 0.0) continue;
+        rmin = min(rmin, lo + c);
+        rmax = max(rmax, lo + c + b - 1);
         const double* v = D0 + (size_t)c * 2 * b;
         double u = 0.0;
         for (int r = c + part; r < c + b; r += 8)
