@@ -14,7 +14,9 @@
 //      stored as (nearest pole, offset) so every d_i - lambda_j is accurate,
 //   3. z recomputed from the roots (Loewner formula, Gu & Eisenstat) so the
 //      eigenvectors u_j ~ z_i / (d_i - lambda_j) are numerically orthogonal,
-//   4. the merged eigenvectors Q [u_j] as one matrix product on the GEMM engine.
+//   4. the merged eigenvectors Q [u_j] as one product per child on the GEMM engine
+//      (the deflation rotations are folded into the rows of [u_j], so Q stays
+//      block diagonal).
 // Eigenvalues of every block are kept sorted ascending.
 #include <math.h>
 
@@ -261,17 +263,19 @@ __global__ void __launch_bounds__(1024) k_prep(int lo, int mid, int hi, const do
   w.rho[0] = rho;
 }
 
-// Deflating rotations applied to the columns of the block, row-parallel, in order.
-__global__ void k_rot(int lo, int hi, double* Z, int ldz, DcWs w, const int* st) {
+// The deflation rotations applied to the rows of U instead of the columns of Q:
+// Q G_0 ... G_{nr-1} U = Q (G_0 (... (G_{nr-1} U))), so Q keeps its block-diagonal
+// form and the merge product splits into one product per child.  One thread per column.
+__global__ void k_rot_u(int lo, int n, double* U, int ldu, DcWs w, const int* st) {
   if (status_bad(st)) return;
-  int r = lo + blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= hi) return;
-  int nr = w.cnt[2];
-  for (int q = 0; q < nr; ++q) {
-    size_t ia = GEP_IX(r, lo + w.ra[q], ldz), ib = GEP_IX(r, lo + w.rb[q], ldz);
-    double x = Z[ia], y = Z[ib], c = w.rc[q], s = w.rs[q];
-    Z[ia] = c * x + s * y;
-    Z[ib] = c * y - s * x;
+  int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= n) return;
+  double* u = U + GEP_IX(lo, lo + col, ldu);
+  for (int q = w.cnt[2] - 1; q >= 0; --q) {
+    int a = w.ra[q], b = w.rb[q];
+    double x = u[a], y = u[b], c = w.rc[q], s = w.rs[q];
+    u[a] = c * x - s * y;
+    u[b] = s * x + c * y;
   }
 }
 
@@ -471,8 +475,6 @@ int tridiag_eig_dc(gep_handle_t h, int M, const double* d, const double* e, doub
       int n = hi - lo;
       k_prep<<<1, 1024, 0, s>>>(lo, mid, hi, e, w.D, Z, ldz, w, stc);
       GEP_CHECK(check_launch(h));
-      k_rot<<<(n + 255) / 256, 256, 0, s>>>(lo, hi, Z, ldz, w, stc);
-      GEP_CHECK(check_launch(h));
       k_secular<<<(n + 7) / 8, 256, 0, s>>>(w, stc);
       GEP_CHECK(check_launch(h));
       k_zhat<<<(n + 127) / 128, 128, 0, s>>>(w, stc);
@@ -484,8 +486,14 @@ int tridiag_eig_dc(gep_handle_t h, int M, const double* d, const double* e, doub
       GEP_CHECK(check_launch(h));
       k_udefl<<<(n + 255) / 256, 256, 0, s>>>(lo, w.U, M, w, stc);
       GEP_CHECK(check_launch(h));
-      GEP_CHECK(dgemm(h, 'N', 'N', 'F', n, n, n, 1.0, Z + GEP_IX(lo, lo, ldz), ldz, w.U + GEP_IX(lo, lo, M), M,
+      k_rot_u<<<(n + 255) / 256, 256, 0, s>>>(lo, n, w.U, M, w, stc);
+      GEP_CHECK(check_launch(h));
+      // Q = diag(Q1, Q2): one product per child (half the flops of a dense n x n product)
+      const int n1 = mid - lo, n2 = hi - mid;
+      GEP_CHECK(dgemm(h, 'N', 'N', 'F', n1, n, n1, 1.0, Z + GEP_IX(lo, lo, ldz), ldz, w.U + GEP_IX(lo, lo, M), M,
                       0.0, w.Qt + GEP_IX(lo, lo, M), M, engine));
+      GEP_CHECK(dgemm(h, 'N', 'N', 'F', n2, n, n2, 1.0, Z + GEP_IX(mid, mid, ldz), ldz, w.U + GEP_IX(mid, lo, M), M,
+                      0.0, w.Qt + GEP_IX(mid, lo, M), M, engine));
       GEP_CHECK(copy_matrix(h, n, n, w.Qt + GEP_IX(lo, lo, M), M, Z + GEP_IX(lo, lo, ldz), ldz));
       k_copy_vec<<<(n + 255) / 256, 256, 0, s>>>(n, w.newD, w.D + lo, stc);
       GEP_CHECK(check_launch(h));
