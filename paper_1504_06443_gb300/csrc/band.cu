@@ -35,6 +35,7 @@ namespace gep {
 namespace {
 
 constexpr int BMAX = 64;      // largest bandwidth
+constexpr int BULGE_CTAS_PER_SM = 1;  // resident bulge-chasing CTAs per SM
 constexpr int PQ_ROWS = 256;  // panel rows per CTA in the panel QR (one per thread)
 constexpr int PQ_CH = 16;     // columns per reduction chunk in the panel QR
 
@@ -215,7 +216,8 @@ __device__ void house(const double* x, int len, double* v, double* out, int b) {
   __syncthreads();
 }
 
-// D (len x len, full, ld BMAX+1) <- H D H, H = I - tau v v^T.
+// D (len x len, full on entry, ld BMAX+1) <- H D H, H = I - tau v v^T; only the lower
+// triangle of the result is formed.
 __device__ void two_sided(double* D, int len, const double* v, double tau, double* p, double* red) {
   const int t = threadIdx.x, i = t & 63, part = t >> 6;
   double s = 0.0;
@@ -235,9 +237,11 @@ __device__ void two_sided(double* D, int len, const double* v, double tau, doubl
   double K = red[4 * BMAX];
   if (t < len) p[t] -= K * v[t];  // w
   __syncthreads();
+  // lower triangle only: the block is stored back as its lower part and re-read (and
+  // mirrored) from the band at every step
   for (int idx = t; idx < len * len; idx += blockDim.x) {
     int a = idx % len, c = idx / len;
-    D[a * (BMAX + 1) + c] -= v[a] * p[c] + p[a] * v[c];
+    if (a >= c) D[a * (BMAX + 1) + c] -= v[a] * p[c] + p[a] * v[c];
   }
   __syncthreads();
 }
@@ -272,7 +276,6 @@ __global__ void __launch_bounds__(256) k_bulge(BulgeArgs a) {
             abort_flag = 1;
             break;
           }
-          __nanosleep(100);
         }
       }
       __syncthreads();
@@ -349,9 +352,11 @@ __global__ void __launch_bounds__(256) k_bulge(BulgeArgs a) {
       }
       if (t < b) vp[t] = vc[t];
       taup = tk;
-      __threadfence();
-      __syncthreads();
-      if (t == 0) st_release(a.prog + s, k + 1);
+      __syncthreads();  // every thread's stores of this step precede the release below
+      if (t == 0) {
+        __threadfence();
+        st_release(a.prog + s, k + 1);
+      }
     }
   }
 }
@@ -648,6 +653,9 @@ int band_to_tridiag(gep_handle_t h, int M, const double* C, int ldc, int b, doub
     int per_sm = 0;
     GEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bulge, 256, smem));
     if (per_sm < 1) return GEP_ERR_UNSUPPORTED;
+    // The sweeps form a dependency chain (step k of sweep s waits for step k+1 of sweep
+    // s-1): the time is set by the latency of one step, which co-resident CTAs stretch.
+    if (per_sm > BULGE_CTAS_PER_SM) per_sm = BULGE_CTAS_PER_SM;
     int grid = per_sm * h->sm_count;
     if (grid > M - 1) grid = M - 1;
     BulgeArgs a;
