@@ -1,18 +1,19 @@
 // SEP solver, stage "BACK" (Table 3): Z <- Q Z with Q = H_0 H_1 ... H_{M-off-1} left
 // in C by the tridiagonalisation (off = 1: reflector j on rows j+1..M-1) or by the
-// full-to-band reduction (off = b: reflector j on rows j+b..M-1).  Reflectors are grouped in panels of NBB and
-// applied from the last panel to the first in compact-WY form,
+// full-to-band reduction (off = b: reflector j on rows j+b..M-1).  Reflectors are
+// grouped in panels of NBB and applied from the last panel to the first in compact-WY
+// form,
 //     H_j ... H_{j+nb-1} = I - V T V^T    (T upper triangular, forward/columnwise),
 //     Z(j+1:, :) -= V (T (V^T Z(j+1:, :))),
-// so all O(M^3) work is three matrix products per panel.  Panels are NBB = 256
-// reflectors wide (the update product then has depth 256); their T factor is built
+// so all O(M^3) work is three matrix products per panel.  Panels are NBB = 512
+// reflectors wide (the update product then has depth 512); their T factor is built
 // recursively, T = [T1, -T1 (V1^T V2) T2; 0, T2], from 64-wide leaves.
 #include "gep_internal.cuh"
 
 namespace gep {
 namespace {
 
-constexpr int NBB = 256;
+constexpr int NBB = 512;
 constexpr int LB = 64;  // leaf order of the T-factor recursion
 
 // Explicit V (rows j0+off .. M-1, nb columns): unit entry at local row q, reflector below.
