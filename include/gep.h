@@ -91,6 +91,9 @@ int gep_set_stream(gep_handle_t h, void* stream);
 
 /* Bytes of device workspace gep_solve needs for order M with options o. */
 int gep_workspace_size(gep_handle_t h, int M, const gep_options* o, size_t* bytes);
+/* Bytes of device workspace that every stage entry point below (gep_cholesky ..
+ * sep_backtransform_2stage) needs for order M and ncol right-hand columns. */
+int gep_stage_workspace_size(gep_handle_t h, int M, int ncol, size_t* bytes);
 /* Hands the library caller-owned device workspace (256-byte aligned).  If none is
  * set, or it is too small, gep_solve returns GEP_ERR_ALLOC. */
 int gep_set_workspace(gep_handle_t h, void* dptr, size_t bytes);

@@ -93,6 +93,7 @@ def load():
             "gep_get_stage_times": (_I, [_P, ctypes.POINTER(_D)]),
             "gep_launch_count": (ctypes.c_longlong, [_P, _I]),
             "gep_refine_steps": (_I, [_P]),
+            "gep_stage_workspace_size": (_I, [_P, _I, _I, ctypes.POINTER(_SZ)]),
             "gep_profile_entry": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
             "gep_get_band_times": (_I, [_P, ctypes.POINTER(_D)]),
             "gep_profile_enable": (_I, [_P, _I]),
@@ -329,16 +330,19 @@ def cholesky(B, handle=None):
     h = handle or default_handle()
     L = colmajor(B.clone())
     M = L.shape[0]
-    h.ensure_workspace(_stage_ws(M))
+    h.ensure_workspace(_stage_ws(M, handle=h))
     h.reset_info()
     _check(h.lib.gep_cholesky(h.h, M, _ptr(L), _ld(L)), "gep_cholesky")
     return L, h.info()
 
 
-def _stage_ws(M, ncol=None):
-    ncol = M if ncol is None else ncol
-    return 8 * (3 * M * M + 2 * M * 128 + ((M + 127) // 128) * 128 * 128 + 64 * M + 1024) + 8 * M * ncol + 4096 + \
-        8 * (M * 64 * 2 + ((M + 63) // 64) * (M + 64) + 64 * 64 * 3)
+def _stage_ws(M, ncol=None, handle=None):
+    """Workspace bytes the stage entry points need (asked from the library)."""
+    h = handle or default_handle()
+    n = _SZ()
+    _check(h.lib.gep_stage_workspace_size(h.h, int(M), int(M if ncol is None else ncol), ctypes.byref(n)),
+           "gep_stage_workspace_size")
+    return n.value
 
 
 def reduce(A, L, variant="twosided", handle=None):
@@ -347,7 +351,7 @@ def reduce(A, L, variant="twosided", handle=None):
     C = colmajor(A.clone())
     Lc = colmajor(L.clone())
     M = C.shape[0]
-    h.ensure_workspace(_stage_ws(M))
+    h.ensure_workspace(_stage_ws(M, handle=h))
     _check(h.lib.gep_reduce(h.h, M, _ptr(C), _ld(C), _ptr(Lc), _ld(Lc), _REDUCERS[variant]), "gep_reduce")
     return C, Lc
 
@@ -358,7 +362,7 @@ def gep_backtransform(LR, Z, variant="twosided", handle=None):
     Y = colmajor(Z.clone())
     Lc = colmajor(LR)
     M, ncol = Y.shape
-    h.ensure_workspace(_stage_ws(M, ncol))
+    h.ensure_workspace(_stage_ws(M, ncol, handle=h))
     _check(h.lib.gep_backtransform(h.h, M, ncol, _ptr(Lc), _ld(Lc), _ptr(Y), _ld(Y), _REDUCERS[variant]),
            "gep_backtransform")
     return Y
@@ -373,7 +377,7 @@ def tridiag_1stage(C, handle=None):
     d = torch.empty(M, dtype=torch.float64, device=C.device)
     e = torch.zeros(max(M, 1), dtype=torch.float64, device=C.device)
     tau = torch.zeros(max(M, 1), dtype=torch.float64, device=C.device)
-    h.ensure_workspace(_stage_ws(M))
+    h.ensure_workspace(_stage_ws(M, handle=h))
     _check(h.lib.sep_tridiag_1stage(h.h, M, _ptr(Cc), _ld(Cc), _ptr(d), _ptr(e), _ptr(tau)), "sep_tridiag_1stage")
     return d, e[: max(M - 1, 0)], tau[: max(M - 1, 0)], Cc
 
@@ -389,7 +393,7 @@ def tridiag_eig(d, e, want_vectors=True, handle=None):
         ee[: M - 1] = e[: M - 1]
     w = torch.empty(M, dtype=torch.float64, device=d.device)
     Zt = torch.empty((M, M), dtype=torch.float64, device=d.device) if want_vectors else None
-    h.ensure_workspace(_stage_ws(M))
+    h.ensure_workspace(_stage_ws(M, handle=h))
     h.reset_info()
     _check(h.lib.sep_tridiag_eig(h.h, M, _ptr(dd), _ptr(ee), _ptr(w), _ptr(Zt), max(1, M), 1 if want_vectors else 0),
            "sep_tridiag_eig")
@@ -406,7 +410,7 @@ def sep_backtransform(C_refl, tau, Z, handle=None):
     tt = torch.zeros(max(M, 1), dtype=torch.float64, device=Z.device)
     if M > 1:
         tt[: M - 1] = tau[: M - 1]
-    h.ensure_workspace(_stage_ws(M, ncol))
+    h.ensure_workspace(_stage_ws(M, ncol, handle=h))
     _check(h.lib.sep_backtransform(h.h, M, ncol, _ptr(Cc), _ld(Cc), _ptr(tt), _ptr(Y), _ld(Y)), "sep_backtransform")
     return Y
 
@@ -442,7 +446,7 @@ def sep_backtransform_2stage(C_refl, tau1, q2, b, Z, handle=None):
     Y = colmajor(Z.clone())
     Cc = colmajor(C_refl)
     M, ncol = Y.shape
-    h.ensure_workspace(max(_two_stage_ws(h, M, b), _stage_ws(M, ncol)))
+    h.ensure_workspace(max(_two_stage_ws(h, M, b), _stage_ws(M, ncol, handle=h)))
     _check(h.lib.sep_backtransform_2stage(h.h, M, ncol, int(b), _ptr(Cc), _ld(Cc), _ptr(tau1.contiguous()),
                                           _ptr(q2), _ptr(Y), _ld(Y)), "sep_backtransform_2stage")
     return Y

@@ -166,6 +166,26 @@ int gep_workspace_size(gep_handle_t h, int M, const gep_options* o, size_t* byte
   return GEP_OK;
 }
 
+int gep_stage_workspace_size(gep_handle_t h, int M, int ncol, size_t* bytes) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (M < 0) return -2;
+  if (ncol < 0) return -3;
+  if (!bytes) return -4;
+  const size_t slack = 4 * 256;  // arena alignment of up to four carvings
+  const size_t d = sizeof(double), mm = (size_t)M * M;
+  size_t need = invd_bytes(M);                                                        // gep_cholesky
+  size_t red = invd_bytes(M) + d * mm + d * (mm + (size_t)NB * M);                    // gep_reduce
+  size_t bks = invd_bytes(M) + d * (size_t)NB * (ncol > M ? ncol : M) + d * mm;       // gep_backtransform
+  size_t tri = d * tridiag_ws_elems(M);
+  size_t dc = dc_ws_bytes(M);
+  size_t bt = d * backtransform_ws_elems(M, ncol > 0 ? ncol : 1);
+  size_t band = d * band_ws_elems(M, 64);                                              // largest bandwidth
+  for (size_t x : {red, bks, tri, dc, bt, band})
+    if (x > need) need = x;
+  *bytes = need + slack;
+  return GEP_OK;
+}
+
 int gep_set_workspace(gep_handle_t h, void* dptr, size_t bytes) {
   if (!handle_ok(h)) return GEP_ERR_HANDLE;
   if (dptr == nullptr && bytes != 0) return -2;

@@ -5,15 +5,15 @@
 // form,
 //     H_j ... H_{j+nb-1} = I - V T V^T    (T upper triangular, forward/columnwise),
 //     Z(j+1:, :) -= V (T (V^T Z(j+1:, :))),
-// so all O(M^3) work is three matrix products per panel.  Panels are NBB = 512
-// reflectors wide (the update product then has depth 512); their T factor is built
+// so all O(M^3) work is three matrix products per panel.  Panels are NBB = 1024
+// reflectors wide (the update product then has depth 1024); their T factor is built
 // recursively, T = [T1, -T1 (V1^T V2) T2; 0, T2], from 64-wide leaves.
 #include "gep_internal.cuh"
 
 namespace gep {
 namespace {
 
-constexpr int NBB = 512;
+constexpr int NBB = 1024;
 constexpr int LB = 64;  // leaf order of the T-factor recursion
 
 // Explicit V (rows j0+off .. M-1, nb columns): unit entry at local row q, reflector below.
