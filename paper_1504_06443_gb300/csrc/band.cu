@@ -141,6 +141,140 @@ __global__ void __launch_bounds__(PQ_ROWS) k_pqr_step(int n, int nb, int c, doub
   }
 }
 
+__device__ __forceinline__ unsigned long long gclock_pq() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// The whole panel QR in one cooperative launch: CTA g keeps panel rows [256 g, 256 g + 256)
+// in shared memory for all column steps, which follow k_pqr_step's arithmetic; the
+// partial dot products and the next pivot row go through part/prow (ping-pong) across a
+// grid barrier.  bar[0] counts barrier arrivals (zero on entry); a barrier that does not
+// complete within 4 s records GEP_ERR_TIMEOUT and the CTA returns.
+__global__ void __launch_bounds__(PQ_ROWS) k_pqr_coop(int n, int nb, double* __restrict__ P, int ldp,
+                                                      double* __restrict__ part0, double* __restrict__ part1,
+                                                      double* __restrict__ prow0, double* __restrict__ prow1,
+                                                      double* __restrict__ tau, int* bar, int* st) {
+  extern __shared__ double Ps[];  // [PQ_ROWS][nb + 1]
+  __shared__ double sd[BMAX], sw[BMAX], sc[3];
+  __shared__ double prod[PQ_ROWS][PQ_CH + 1];
+  __shared__ double seg[PQ_ROWS / PQ_CH][PQ_CH];
+  __shared__ int gok;
+  if (status_bad(st)) return;
+  const int t = threadIdx.x, G = gridDim.x, blk = blockIdx.x;
+  const int r = blk * PQ_ROWS + t;
+  const int ld = nb + 1;
+  for (int j = 0; j < nb; ++j) Ps[t * ld + j] = (r < n) ? P[r + (size_t)j * ldp] : 0.0;
+  const int nref = n < nb ? n : nb;
+  double *pin = part0, *pout = part1, *rin = prow0, *rout = prow1;
+  int epoch = 0;
+  __syncthreads();
+  for (int c = -1; c < nref; ++c) {
+    double tk = 0.0, scale = 0.0, beta = 0.0;
+    if (c >= 0) {
+      {  // column j's partials pin[j * G + g], one warp per column, fixed-order tree
+        const int w = t >> 5, lane = t & 31;
+        for (int j = c + w; j < nb; j += PQ_ROWS / 32) {
+          double s = 0.0;
+          for (int g = lane; g < G; g += 32) s += __ldcg(pin + (size_t)j * G + g);
+          for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          if (lane == 0) sd[j] = s;
+        }
+      }
+      __syncthreads();
+      if (t == 0) {
+        double alpha = __ldcg(rin + c), xn2 = sd[c];
+        double tt = 0.0, sl = 0.0, be = alpha;
+        if (xn2 > 0.0) {
+          be = -copysign(sqrt(alpha * alpha + xn2), alpha);
+          tt = (be - alpha) / be;
+          sl = 1.0 / (alpha - be);
+        }
+        sc[0] = tt;
+        sc[1] = sl;
+        sc[2] = be;
+        if (blk == 0) tau[c] = tt;
+      }
+      __syncthreads();
+      tk = sc[0];
+      scale = sc[1];
+      beta = sc[2];
+      if (t < nb && t > c) sw[t] = __ldcg(rin + t) + scale * sd[t];  // v^T P(:, t)
+      __syncthreads();
+    }
+    const int nc = c + 1;
+    const bool live = r < n && r >= (c < 0 ? 0 : c);
+    double* row = Ps + t * ld;
+    if (live && c >= 0) {
+      const double vr = (r == c) ? 1.0 : row[c] * scale;
+      row[c] = (r == c) ? beta : vr;
+      for (int j = c + 1; j < nb; ++j) row[j] -= tk * vr * sw[j];
+    }
+    if (nc < nb) {
+      const double pn = (live && r > nc) ? row[nc] : 0.0;
+      for (int cb = nc; cb < nb; cb += PQ_CH) {
+        for (int q = 0; q < PQ_CH; ++q) {
+          int j = cb + q;
+          double pr = 0.0;
+          if (live && j < nb) {
+            if (r == nc) rout[j] = row[j];
+            if (r > nc) pr = pn * row[j];
+          }
+          prod[t][q] = pr;
+        }
+        __syncthreads();
+        {
+          int q = t % PQ_CH, sg = t / PQ_CH;
+          double sum = 0.0;
+          for (int i = 0; i < PQ_CH; ++i) sum += prod[sg * PQ_CH + i][q];
+          seg[sg][q] = sum;
+        }
+        __syncthreads();
+        if (t < PQ_CH && cb + t < nb) {
+          double sum = 0.0;
+          for (int sg = 0; sg < PQ_ROWS / PQ_CH; ++sg) sum += seg[sg][t];
+          pout[(size_t)(cb + t) * G + blk] = sum;
+        }
+        __syncthreads();
+      }
+    }
+    if (c + 1 >= nref) break;  // the last step needs no exchange
+    // grid barrier: this CTA's pout / rout are complete and visible before any CTA reads them
+    __syncthreads();
+    if (t == 0) {
+      __threadfence();
+      const int target = (epoch + 1) * G;
+      int ok = 1;
+      if (atomicAdd(bar, 1) + 1 < target) {
+        unsigned long long t0 = gclock_pq();
+        for (;;) {
+          int v;
+          asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+          if (v >= target) break;
+          if (*(volatile int*)(st + 1) != 0) { ok = 0; break; }
+          if (gclock_pq() - t0 > 4000000000ull) {
+            atomicExch(st + 1, GEP_ERR_TIMEOUT);
+            ok = 0;
+            break;
+          }
+        }
+      }
+      gok = ok;
+    }
+    __syncthreads();
+    if (!gok) return;
+    ++epoch;
+    double* tp = pin; pin = pout; pout = tp;
+    tp = rin; rin = rout; rout = tp;
+  }
+  __syncthreads();
+  if (r < n)
+    for (int j = 0; j < nb; ++j) P[r + (size_t)j * ldp] = Ps[t * ld + j];
+}
+
+size_t pqr_coop_smem_bytes(int nb) { return (size_t)PQ_ROWS * (nb + 1) * sizeof(double); }
+
 // V (n x nb, ld n): unit lower trapezoidal factor of the panel QR stored in P.
 __global__ void k_panel_v(int n, int nb, const double* __restrict__ P, int ldp, double* __restrict__ V,
                           const int* st) {
@@ -506,7 +640,7 @@ size_t q2_elems(int M, int b) {
 
 size_t band_ws_elems(int M, int b) {
   size_t G = ((size_t)M + PQ_ROWS - 1) / PQ_ROWS;
-  size_t reduce = 2 * rr(G * BMAX) + 2 * rr(BMAX) + 4 * rr((size_t)M * b) + rr((size_t)M * 3 * b) +
+  size_t reduce = 2 * rr(G * BMAX) + 2 * rr(BMAX) + rr(32) + 4 * rr((size_t)M * b) + rr((size_t)M * 3 * b) +
                   2 * rr((size_t)M * 4 * b) + 6 * rr((size_t)2 * b * b);
   size_t chase = rr((size_t)2 * b * M) + rr((size_t)M);  // band + progress counters
   return reduce > chase ? reduce : chase;
@@ -516,6 +650,7 @@ namespace {
 
 struct BandWs {
   double *part0, *part1, *prow0, *prow1;
+  int* bar;
   double *V, *CV, *WVW, *V1, *W1, *AA, *BB;
   double *GV, *T, *Tt, *Pm, *Ym, *Zs;
 };
@@ -527,13 +662,30 @@ int panel_factor(gep_handle_t h, int n, int b, double* P, int ldp, double* tau, 
   const int G = (n + PQ_ROWS - 1) / PQ_ROWS;
   const int nref = n < b ? n : b;
   double *pin = w.part0, *pout = w.part1, *rin = w.prow0, *rout = w.prow1;
-  k_pqr_step<<<G, PQ_ROWS, 0, h->stream>>>(n, b, -1, P, ldp, pin, rin, pout, rout, tau, h->d_status);
-  GEP_CHECK(check_launch(h));
-  for (int c = 0; c < nref; ++c) {
-    double* tp = pin; pin = pout; pout = tp;
-    tp = rin; rin = rout; rout = tp;
-    k_pqr_step<<<G, PQ_ROWS, 0, h->stream>>>(n, b, c, P, ldp, pin, rin, pout, rout, tau, h->d_status);
+  // one cooperative launch when every CTA of the panel can be resident at once
+  static int coop_per_sm = -1;
+  const size_t smem = pqr_coop_smem_bytes(BMAX);
+  if (coop_per_sm < 0) {
+    GEP_CUDA(cudaFuncSetAttribute(k_pqr_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&coop_per_sm, k_pqr_coop, PQ_ROWS, smem));
+  }
+  if (coop_per_sm > 0 && G <= coop_per_sm * h->sm_count) {
+    GEP_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(int), h->stream));
+    int nn = n, nbb = b, ld = ldp;
+    int* bar = w.bar;
+    int* st = h->d_status;
+    void* args[] = {&nn, &nbb, &P, &ld, &pin, &pout, &rin, &rout, &tau, &bar, &st};
+    GEP_CUDA(cudaLaunchCooperativeKernel((void*)k_pqr_coop, dim3(G), dim3(PQ_ROWS), args, smem, h->stream));
     GEP_CHECK(check_launch(h));
+  } else {
+    k_pqr_step<<<G, PQ_ROWS, 0, h->stream>>>(n, b, -1, P, ldp, pin, rin, pout, rout, tau, h->d_status);
+    GEP_CHECK(check_launch(h));
+    for (int c = 0; c < nref; ++c) {
+      double* tp = pin; pin = pout; pout = tp;
+      tp = rin; rin = rout; rout = tp;
+      k_pqr_step<<<G, PQ_ROWS, 0, h->stream>>>(n, b, c, P, ldp, pin, rin, pout, rout, tau, h->d_status);
+      GEP_CHECK(check_launch(h));
+    }
   }
   k_panel_v<<<dim3((n + 255) / 256, b), 256, 0, h->stream>>>(n, b, P, ldp, V, h->d_status);
   GEP_CHECK(check_launch(h));
@@ -573,6 +725,7 @@ int band_reduce(gep_handle_t h, int M, double* C, int ldc, int b, double* tau1, 
   w.part1 = take(Gmax * BMAX);
   w.prow0 = take(BMAX);
   w.prow1 = take(BMAX);
+  w.bar = reinterpret_cast<int*>(take(32));
   w.V = take((size_t)M * b);
   w.CV = take((size_t)M * b);
   w.V1 = take((size_t)M * b);
