@@ -141,31 +141,43 @@ __global__ void __launch_bounds__(PQ_ROWS) k_pqr_step(int n, int nb, int c, doub
   }
 }
 
-__device__ __forceinline__ unsigned long long gclock_pq() {
+__device__ __forceinline__ unsigned long long gclock() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
-// The whole panel QR in one cooperative launch: CTA g keeps panel rows [256 g, 256 g + 256)
-// in shared memory for all column steps, which follow k_pqr_step's arithmetic; the
+// The whole panel QR in one cooperative launch: CTA g keeps panel rows [rp g, rp g + rp)
+// (rp = 64, 128 or 256: the per-SM FP64 rate bounds a step, so short panels take more
+// CTAs of fewer rows) in shared memory for all column steps, which follow k_pqr_step's
+// arithmetic; the
 // partial dot products and the next pivot row go through part/prow (ping-pong) across a
 // grid barrier.  bar[0] counts barrier arrivals (zero on entry); a barrier that does not
 // complete within 4 s records GEP_ERR_TIMEOUT and the CTA returns.
-__global__ void __launch_bounds__(PQ_ROWS) k_pqr_coop(int n, int nb, double* __restrict__ P, int ldp,
+__global__ void __launch_bounds__(PQ_ROWS) k_pqr_coop(int n, int nb, int rp, double* __restrict__ P, int ldp,
                                                       double* __restrict__ part0, double* __restrict__ part1,
                                                       double* __restrict__ prow0, double* __restrict__ prow1,
                                                       double* __restrict__ tau, int* bar, int* st) {
-  extern __shared__ double Ps[];  // [PQ_ROWS][nb + 1]
+  extern __shared__ double Ps[];  // [rp][nb + 1]
   __shared__ double sd[BMAX], sw[BMAX], sc[3];
   __shared__ double prod[PQ_ROWS][PQ_CH + 1];
   __shared__ double seg[PQ_ROWS / PQ_CH][PQ_CH];
   __shared__ int gok;
   if (status_bad(st)) return;
   const int t = threadIdx.x, G = gridDim.x, blk = blockIdx.x;
-  const int r = blk * PQ_ROWS + t;
+  const bool mine = t < rp;
+  const int r = blk * rp + t;
   const int ld = nb + 1;
-  for (int j = 0; j < nb; ++j) Ps[t * ld + j] = (r < n) ? P[r + (size_t)j * ldp] : 0.0;
+  if (mine)
+    for (int j = 0; j < nb; ++j) Ps[t * ld + j] = (r < n) ? P[r + (size_t)j * ldp] : 0.0;
   const int nref = n < nb ? n : nb;
   double *pin = part0, *pout = part1, *rin = prow0, *rout = prow1;
   int epoch = 0;
@@ -204,7 +216,7 @@ __global__ void __launch_bounds__(PQ_ROWS) k_pqr_coop(int n, int nb, double* __r
       __syncthreads();
     }
     const int nc = c + 1;
-    const bool live = r < n && r >= (c < 0 ? 0 : c);
+    const bool live = mine && r < n && r >= (c < 0 ? 0 : c);
     double* row = Ps + t * ld;
     if (live && c >= 0) {
       const double vr = (r == c) ? 1.0 : row[c] * scale;
@@ -221,10 +233,10 @@ __global__ void __launch_bounds__(PQ_ROWS) k_pqr_coop(int n, int nb, double* __r
             if (r == nc) rout[j] = row[j];
             if (r > nc) pr = pn * row[j];
           }
-          prod[t][q] = pr;
+          if (mine) prod[t][q] = pr;
         }
         __syncthreads();
-        {
+        if (t < rp) {
           int q = t % PQ_CH, sg = t / PQ_CH;
           double sum = 0.0;
           for (int i = 0; i < PQ_CH; ++i) sum += prod[sg * PQ_CH + i][q];
@@ -233,7 +245,7 @@ __global__ void __launch_bounds__(PQ_ROWS) k_pqr_coop(int n, int nb, double* __r
         __syncthreads();
         if (t < PQ_CH && cb + t < nb) {
           double sum = 0.0;
-          for (int sg = 0; sg < PQ_ROWS / PQ_CH; ++sg) sum += seg[sg][t];
+          for (int sg = 0; sg < rp / PQ_CH; ++sg) sum += seg[sg][t];
           pout[(size_t)(cb + t) * G + blk] = sum;
         }
         __syncthreads();
@@ -247,13 +259,11 @@ __global__ void __launch_bounds__(PQ_ROWS) k_pqr_coop(int n, int nb, double* __r
       const int target = (epoch + 1) * G;
       int ok = 1;
       if (atomicAdd(bar, 1) + 1 < target) {
-        unsigned long long t0 = gclock_pq();
+        unsigned long long t0 = gclock();
         for (;;) {
-          int v;
-          asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
-          if (v >= target) break;
+          if (ld_acquire(bar) >= target) break;
           if (*(volatile int*)(st + 1) != 0) { ok = 0; break; }
-          if (gclock_pq() - t0 > 4000000000ull) {
+          if (gclock() - t0 > 4000000000ull) {
             atomicExch(st + 1, GEP_ERR_TIMEOUT);
             ok = 0;
             break;
@@ -269,11 +279,11 @@ __global__ void __launch_bounds__(PQ_ROWS) k_pqr_coop(int n, int nb, double* __r
     tp = rin; rin = rout; rout = tp;
   }
   __syncthreads();
-  if (r < n)
+  if (mine && r < n)
     for (int j = 0; j < nb; ++j) P[r + (size_t)j * ldp] = Ps[t * ld + j];
 }
 
-size_t pqr_coop_smem_bytes(int nb) { return (size_t)PQ_ROWS * (nb + 1) * sizeof(double); }
+size_t pqr_coop_smem_bytes(int rp, int nb) { return (size_t)rp * (nb + 1) * sizeof(double); }
 
 // V (n x nb, ld n): unit lower trapezoidal factor of the panel QR stored in P.
 __global__ void k_panel_v(int n, int nb, const double* __restrict__ P, int ldp, double* __restrict__ V,
@@ -293,20 +303,6 @@ __global__ void k_band_copy(int M, int b, const double* __restrict__ C, int ldc,
   int o = threadIdx.x, j = blockIdx.x;
   if (o >= ldab || j >= M) return;
   AB[o + (size_t)j * ldab] = (o <= b && j + o < M) ? C[(j + o) + (size_t)j * ldc] : 0.0;
-}
-
-__device__ __forceinline__ unsigned long long gclock() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(int* p, int v) {
-  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ int bulge_steps(int M, int b, int s) { return (M - 2 - s) / b + 1; }
@@ -332,16 +328,15 @@ __device__ void house(const double* x, int len, double* v, double* out, int b) {
     double s = 0.0;
     for (int i = 1 + t; i < len; i += 32) s += x[i] * x[i];
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (t == 0) {
-      double alpha = x[0], tt = 0.0, sl = 0.0, be = alpha;
+    if (t < 2) {  // lane 0 forms tau, lane 1 the scale: one division sequence for both
+      double alpha = x[0], be = alpha, q = 0.0;
       if (s > 0.0) {
         be = -copysign(sqrt(alpha * alpha + s), alpha);
-        tt = (be - alpha) / be;
-        sl = 1.0 / (alpha - be);
+        const double num = (t == 0) ? be - alpha : 1.0, den = (t == 0) ? be : alpha - be;
+        q = num / den;
       }
-      out[0] = tt;
-      out[1] = be;
-      out[2] = sl;
+      out[t == 0 ? 0 : 2] = q;
+      if (t == 0) out[1] = be;
     }
   }
   __syncthreads();
@@ -380,6 +375,89 @@ __device__ void two_sided(double* D, int len, const double* v, double tau, doubl
   __syncthreads();
 }
 
+// One chasing step k >= 1 of a full block (b = len = BMAX = 64, 256 threads), the same
+// arithmetic as the general step below with a fixed thread map: thread t owns row
+// i = t mod 64 and columns q = t / 64 + 4 r (r < 16) of B and of the diagonal block D.
+// B and the lower triangle of D are fetched in one round of coalesced loads.
+__device__ __forceinline__ void bulge_step_full(const BulgeArgs& a, int stp, int st_k, double* Bm, double* Dm,
+                                                const double* vp, double* vc, double* xv, double* pw, double* red,
+                                                double* hs, double taup) {
+  constexpr int N = BMAX, LD = BMAX + 1, R = N / 4;
+  const int t = threadIdx.x, i = t & (N - 1), part = t >> 6;
+  const int ldab = a.ldab;
+  const double* AB = a.AB;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int q = part + 4 * r;
+    Bm[i * LD + q] = __ldcg(AB + (N + i - q) + (size_t)(stp + q) * ldab);
+    if (q <= i) Dm[i * LD + q] = __ldcg(AB + (i - q) + (size_t)(st_k + q) * ldab);
+  }
+  __syncthreads();
+  {  // B <- B H(s, k-1): y = B vp, B -= taup y vp^T (the thread's own row: no barrier between)
+    double y = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) y += Bm[i * LD + part + 4 * r] * vp[part + 4 * r];
+    red[part * N + i] = y;
+    __syncthreads();
+    const double yi = taup * (red[i] + red[N + i] + red[2 * N + i] + red[3 * N + i]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) Bm[i * LD + part + 4 * r] -= yi * vp[part + 4 * r];
+    if (part == 0) xv[i] = Bm[i * LD];
+  }
+  __syncthreads();
+  house(xv, N, vc, hs, N);
+  const double tk = hs[0];
+  {  // B(:, 1:) <- H B(:, 1:): u = tau B^T v over rows i = part + 4 r
+    const int q = i;
+    double u = 0.0;
+    if (q >= 1)
+#pragma unroll
+      for (int r = 0; r < R; ++r) u += vc[part + 4 * r] * Bm[(part + 4 * r) * LD + q];
+    red[part * N + q] = u;
+    __syncthreads();
+    if (t < N) pw[t] = tk * (red[t] + red[N + t] + red[2 * N + t] + red[3 * N + t]);
+    __syncthreads();
+    const double beta = hs[1];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int qq = part + 4 * r;
+      const double x = (qq == 0) ? (i == 0 ? beta : 0.0) : Bm[i * LD + qq] - vc[i] * pw[qq];
+      a.AB[(N + i - qq) + (size_t)(stp + qq) * ldab] = x;
+    }
+  }
+  {  // D <- H D H on the lower triangle (D read symmetric from its lower half)
+    double y = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int q = part + 4 * r;
+      y += (q <= i ? Dm[i * LD + q] : Dm[q * LD + i]) * vc[q];
+    }
+    red[part * N + i] = y;
+    __syncthreads();
+    if (t < N) pw[t] = tk * (red[t] + red[N + t] + red[2 * N + t] + red[3 * N + t]);
+    __syncthreads();
+    if (t < 32) {  // K = tau/2 p^T v
+      double kk = 0.0;
+      for (int q = t; q < N; q += 32) kk += pw[q] * vc[q];
+      for (int o = 16; o; o >>= 1) kk += __shfl_xor_sync(0xffffffffu, kk, o);
+      if (t == 0) red[4 * N] = 0.5 * tk * kk;
+    }
+    __syncthreads();
+    const double K = red[4 * N];
+    if (t < N) pw[t] -= K * vc[t];
+    __syncthreads();
+    const double vi = vc[i], wi = pw[i];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int q = part + 4 * r;
+      if (q <= i) {
+        const double x = Dm[i * LD + q] - (vi * pw[q] + wi * vc[q]);
+        a.AB[(i - q) + (size_t)(st_k + q) * ldab] = x;
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_bulge(BulgeArgs a) {
   extern __shared__ double sm[];
   double* Bm = sm;                          // BMAX x (BMAX+1), [row][col]
@@ -416,68 +494,73 @@ __global__ void __launch_bounds__(256) k_bulge(BulgeArgs a) {
       if (abort_flag) return;
       const int st_k = s + 1 + k * b;
       const int len = (M - st_k) < b ? (M - st_k) : b;
-      if (k == 0) {
-        for (int i = t; i < len; i += blockDim.x) xv[i] = __ldcg(a.AB + (1 + i) + (size_t)s * ldab);
-        __syncthreads();
-        house(xv, len, vc, hs, b);
-        if (t < len) a.AB[(1 + t) + (size_t)s * ldab] = (t == 0) ? hs[1] : 0.0;
+      if (k > 0 && b == BMAX && len == BMAX) {
+        bulge_step_full(a, st_k - b, st_k, Bm, Dm, vp, vc, xv, pw, red, hs, taup);
       } else {
-        const int stp = st_k - b;  // previous block's first row/column (its length is b)
-        for (int idx = t; idx < len * b; idx += blockDim.x) {
+        if (k == 0) {
+          for (int i = t; i < len; i += blockDim.x) xv[i] = __ldcg(a.AB + (1 + i) + (size_t)s * ldab);
+          __syncthreads();
+          house(xv, len, vc, hs, b);
+          if (t < len) a.AB[(1 + t) + (size_t)s * ldab] = (t == 0) ? hs[1] : 0.0;
+        } else {
+          const int stp = st_k - b;  // previous block's first row/column (its length is b)
+          for (int idx = t; idx < len * b; idx += blockDim.x) {
+            int i = idx % len, q = idx / len;
+            Bm[i * (BMAX + 1) + q] = __ldcg(a.AB + (b + i - q) + (size_t)(stp + q) * ldab);
+          }
+          __syncthreads();
+          {  // B <- B H(s,k-1): y = B vp, B -= taup y vp^T
+            int i = t & 63, part = t >> 6;
+            double y = 0.0;
+            if (i < len)
+              for (int q = part; q < b; q += 4) y += Bm[i * (BMAX + 1) + q] * vp[q];
+            red[part * BMAX + i] = y;
+            __syncthreads();
+            if (t < len) pw[t] = taup * (red[t] + red[BMAX + t] + red[2 * BMAX + t] + red[3 * BMAX + t]);
+            __syncthreads();
+            for (int idx = t; idx < len * b; idx += blockDim.x) {
+              int ii = idx % len, q = idx / len;
+              Bm[ii * (BMAX + 1) + q] -= pw[ii] * vp[q];
+            }
+            __syncthreads();
+          }
+          for (int i = t; i < len; i += blockDim.x) xv[i] = Bm[i * (BMAX + 1)];
+          __syncthreads();
+          house(xv, len, vc, hs, b);
+          {  // B(:, 1:) <- H B(:, 1:): u = tau B^T v
+            double tk = hs[0];
+            int q = t & 63, part = t >> 6;
+            double u = 0.0;
+            if (q >= 1 && q < b)
+              for (int i = part; i < len; i += 4) u += vc[i] * Bm[i * (BMAX + 1) + q];
+            red[part * BMAX + q] = u;
+            __syncthreads();
+            if (t < b) pw[t] = tk * (red[t] + red[BMAX + t] + red[2 * BMAX + t] + red[3 * BMAX + t]);
+            __syncthreads();
+            for (int idx = t; idx < len * b; idx += blockDim.x) {
+              int i = idx % len, qq = idx / len;
+              double x;
+              if (qq == 0) x = (i == 0) ? hs[1] : 0.0;
+              else x = Bm[i * (BMAX + 1) + qq] - vc[i] * pw[qq];
+              a.AB[(b + i - qq) + (size_t)(stp + qq) * ldab] = x;
+            }
+          }
+        }
+        // D = C(st_k : st_k+len, same) <- H D H
+        for (int idx = t; idx < len * len; idx += blockDim.x) {
           int i = idx % len, q = idx / len;
-          Bm[i * (BMAX + 1) + q] = __ldcg(a.AB + (b + i - q) + (size_t)(stp + q) * ldab);
+          int lo = i > q ? i : q, hi = i > q ? q : i;
+          Dm[i * (BMAX + 1) + q] = __ldcg(a.AB + (lo - hi) + (size_t)(st_k + hi) * ldab);
         }
         __syncthreads();
-        {  // B <- B H(s,k-1): y = B vp, B -= taup y vp^T
-          int i = t & 63, part = t >> 6;
-          double y = 0.0;
-          if (i < len)
-            for (int q = part; q < b; q += 4) y += Bm[i * (BMAX + 1) + q] * vp[q];
-          red[part * BMAX + i] = y;
-          __syncthreads();
-          if (t < len) pw[t] = taup * (red[t] + red[BMAX + t] + red[2 * BMAX + t] + red[3 * BMAX + t]);
-          __syncthreads();
-          for (int idx = t; idx < len * b; idx += blockDim.x) {
-            int ii = idx % len, q = idx / len;
-            Bm[ii * (BMAX + 1) + q] -= pw[ii] * vp[q];
-          }
-          __syncthreads();
-        }
-        for (int i = t; i < len; i += blockDim.x) xv[i] = Bm[i * (BMAX + 1)];
-        __syncthreads();
-        house(xv, len, vc, hs, b);
-        {  // B(:, 1:) <- H B(:, 1:): u = tau B^T v
-          double tk = hs[0];
-          int q = t & 63, part = t >> 6;
-          double u = 0.0;
-          if (q >= 1 && q < b)
-            for (int i = part; i < len; i += 4) u += vc[i] * Bm[i * (BMAX + 1) + q];
-          red[part * BMAX + q] = u;
-          __syncthreads();
-          if (t < b) pw[t] = tk * (red[t] + red[BMAX + t] + red[2 * BMAX + t] + red[3 * BMAX + t]);
-          __syncthreads();
-          for (int idx = t; idx < len * b; idx += blockDim.x) {
-            int i = idx % len, qq = idx / len;
-            double x;
-            if (qq == 0) x = (i == 0) ? hs[1] : 0.0;
-            else x = Bm[i * (BMAX + 1) + qq] - vc[i] * pw[qq];
-            a.AB[(b + i - qq) + (size_t)(stp + qq) * ldab] = x;
-          }
+        double tk = hs[0];
+        two_sided(Dm, len, vc, tk, pw, red);
+        for (int idx = t; idx < len * len; idx += blockDim.x) {
+          int i = idx % len, q = idx / len;
+          if (i >= q) a.AB[(i - q) + (size_t)(st_k + q) * ldab] = Dm[i * (BMAX + 1) + q];
         }
       }
-      // D = C(st_k : st_k+len, same) <- H D H
-      for (int idx = t; idx < len * len; idx += blockDim.x) {
-        int i = idx % len, q = idx / len;
-        int lo = i > q ? i : q, hi = i > q ? q : i;
-        Dm[i * (BMAX + 1) + q] = __ldcg(a.AB + (lo - hi) + (size_t)(st_k + hi) * ldab);
-      }
-      __syncthreads();
-      double tk = hs[0];
-      two_sided(Dm, len, vc, tk, pw, red);
-      for (int idx = t; idx < len * len; idx += blockDim.x) {
-        int i = idx % len, q = idx / len;
-        if (i >= q) a.AB[(i - q) + (size_t)(st_k + q) * ldab] = Dm[i * (BMAX + 1) + q];
-      }
+      const double tk = hs[0];
       if (a.q2) {  // reflector into diamond (j, k), column c
         int j = s / b, c = s - j * b;
         double* D0 = a.q2 + diamond_index(a.Q, j, k) * diamond_elems(b);
@@ -632,6 +715,14 @@ size_t bulge_smem_bytes() { return ((size_t)2 * BMAX * (BMAX + 1) + 4 * BMAX + 4
 
 }  // namespace
 
+// CTAs whose partial sums the panel-QR buffers hold: the per-step kernel's ceil(M / 256),
+// or up to 1024 CTAs of 64 rows for the single-launch form.
+static size_t pqr_partial_ctas(int M) {
+  size_t g256 = ((size_t)M + PQ_ROWS - 1) / PQ_ROWS, g64 = ((size_t)M + 63) / 64;
+  if (g64 > 1024) g64 = 1024;
+  return g256 > g64 ? g256 : g64;
+}
+
 size_t q2_elems(int M, int b) {
   if (M < 2 || b < 1) return 0;
   size_t Q = (size_t)(M - 2) / b;
@@ -639,7 +730,7 @@ size_t q2_elems(int M, int b) {
 }
 
 size_t band_ws_elems(int M, int b) {
-  size_t G = ((size_t)M + PQ_ROWS - 1) / PQ_ROWS;
+  size_t G = pqr_partial_ctas(M);
   size_t reduce = 2 * rr(G * BMAX) + 2 * rr(BMAX) + rr(32) + 4 * rr((size_t)M * b) + rr((size_t)M * 3 * b) +
                   2 * rr((size_t)M * 4 * b) + 6 * rr((size_t)2 * b * b);
   size_t chase = rr((size_t)2 * b * M) + rr((size_t)M);  // band + progress counters
@@ -650,6 +741,7 @@ namespace {
 
 struct BandWs {
   double *part0, *part1, *prow0, *prow1;
+  long long gcap;  // CTAs the partial-sum buffers hold
   int* bar;
   double *V, *CV, *WVW, *V1, *W1, *AA, *BB;
   double *GV, *T, *Tt, *Pm, *Ym, *Zs;
@@ -664,18 +756,27 @@ int panel_factor(gep_handle_t h, int n, int b, double* P, int ldp, double* tau, 
   double *pin = w.part0, *pout = w.part1, *rin = w.prow0, *rout = w.prow1;
   // one cooperative launch when every CTA of the panel can be resident at once
   static int coop_per_sm = -1;
-  const size_t smem = pqr_coop_smem_bytes(BMAX);
   if (coop_per_sm < 0) {
-    GEP_CUDA(cudaFuncSetAttribute(k_pqr_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    GEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&coop_per_sm, k_pqr_coop, PQ_ROWS, smem));
+    const size_t smax = pqr_coop_smem_bytes(PQ_ROWS, BMAX);
+    GEP_CUDA(cudaFuncSetAttribute(k_pqr_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+    GEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&coop_per_sm, k_pqr_coop, PQ_ROWS, smax));
   }
-  if (coop_per_sm > 0 && G <= coop_per_sm * h->sm_count) {
+  // fewest rows per CTA whose grid is resident at once and fits the partial-sum buffers
+  const long long cap = (long long)coop_per_sm * h->sm_count;
+  int rp = 0;
+  for (int c = 64; c <= PQ_ROWS; c *= 2) {
+    long long g = (n + c - 1) / c;
+    if (g <= cap && g <= w.gcap) { rp = c; break; }
+  }
+  if (rp > 0) {
+    const int Gc = (n + rp - 1) / rp;
+    const size_t smem = pqr_coop_smem_bytes(rp, BMAX);
     GEP_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(int), h->stream));
-    int nn = n, nbb = b, ld = ldp;
+    int nn = n, nbb = b, rpp = rp, ld = ldp;
     int* bar = w.bar;
     int* st = h->d_status;
-    void* args[] = {&nn, &nbb, &P, &ld, &pin, &pout, &rin, &rout, &tau, &bar, &st};
-    GEP_CUDA(cudaLaunchCooperativeKernel((void*)k_pqr_coop, dim3(G), dim3(PQ_ROWS), args, smem, h->stream));
+    void* args[] = {&nn, &nbb, &rpp, &P, &ld, &pin, &pout, &rin, &rout, &tau, &bar, &st};
+    GEP_CUDA(cudaLaunchCooperativeKernel((void*)k_pqr_coop, dim3(Gc), dim3(PQ_ROWS), args, smem, h->stream));
     GEP_CHECK(check_launch(h));
   } else {
     k_pqr_step<<<G, PQ_ROWS, 0, h->stream>>>(n, b, -1, P, ldp, pin, rin, pout, rout, tau, h->d_status);
@@ -717,8 +818,9 @@ int band_reduce(gep_handle_t h, int M, double* C, int ldc, int b, double* tau1, 
   if (M <= 0) return GEP_OK;
   GEP_CHECK(set_matrix(h, M, 1, 0.0, 0.0, tau1, M));
   if (M <= b + 1) return GEP_OK;
-  size_t Gmax = ((size_t)M + PQ_ROWS - 1) / PQ_ROWS;
+  size_t Gmax = pqr_partial_ctas(M);
   BandWs w;
+  w.gcap = (long long)Gmax;
   double* q = ws;
   auto take = [&](size_t n) { double* p = q; q += rr(n); return p; };
   w.part0 = take(Gmax * BMAX);

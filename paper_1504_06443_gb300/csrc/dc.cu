@@ -30,7 +30,9 @@ constexpr double EPS = 0x1p-53;
 
 struct DcWs {
   double *Qt, *U, *D, *dd, *zs, *dv, *ndd, *ndz, *dfv, *rc, *rs, *tauR, *lam, *zhat, *newD, *rho;
+  double *ptau, *pc, *ps;  // the Givens deflation test of each adjacent pair, from the undeflated values
   int *perm, *ndx, *dfx, *ra, *rb, *org, *posr, *posd, *cnt;
+  int *nsl, *prot;         // positions (in perm) with z not negligible; pair test outcome
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -182,18 +184,24 @@ __global__ void __launch_bounds__(128) k_leaf(int M, const double* __restrict__ 
   if (lane < n) D[lo + lane] = dl[w][ord[w][lane]];
 }
 
-// Merge set-up (one CTA): z, sort of the two halves' eigenvalues, deflation.
+// Merge set-up (one CTA): z, sort of the two halves' eigenvalues, deflation.  The
+// deflation scan is sequential (a Givens rotation changes the next pair's operands), but
+// only a rotated pair's successor needs its test re-evaluated: every pair's test is first
+// formed in parallel from the undeflated values, and the scan takes those results wherever
+// the previous pair was not rotated, which gives the sequential outcome exactly.
 __global__ void __launch_bounds__(1024) k_prep(int lo, int mid, int hi, const double* __restrict__ e,
                                                const double* __restrict__ D, const double* __restrict__ Z,
                                                int ldz, DcWs w, const int* st) {
   __shared__ double red[32];
+  __shared__ int scnt[1024];
   if (status_bad(st)) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
   int n = hi - lo, n1 = mid - lo;
   double beta = e[mid - 1];
   double sg = beta < 0.0 ? -1.0 : 1.0;
   double rho = 2.0 * fabs(beta);
   double zmax = 0.0, dmax = 0.0;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+  for (int t = tid; t < n; t += nt) {
     double z = (t < n1) ? Z[GEP_IX(mid - 1, lo + t, ldz)] : sg * Z[GEP_IX(mid, lo + t, ldz)];
     z *= 0.70710678118654752440;
     w.zs[t] = z;
@@ -205,14 +213,51 @@ __global__ void __launch_bounds__(1024) k_prep(int lo, int mid, int hi, const do
   zmax = block_max(zmax, red);
   dmax = block_max(dmax, red);
   __syncthreads();
-  if (threadIdx.x != 0) return;
   const double tol = 8.0 * EPS * 2.0 * fmax(dmax, zmax);
-  // merge the two ascending runs [0, n1) and [n1, n)
-  int a = 0, b = n1, o = 0;
-  while (a < n1 && b < n) w.perm[o++] = (w.dv[a] <= w.dv[b]) ? a++ : b++;
-  while (a < n1) w.perm[o++] = a++;
-  while (b < n) w.perm[o++] = b++;
-  int k = 0, nd = 0, nr = 0, pj = -1;
+  // merge the two ascending runs [0, n1) and [n1, n), the first run's entry first on ties
+  for (int x = tid; x < n; x += nt) {
+    const double v = w.dv[x];
+    int a = (x < n1) ? n1 : 0, b = (x < n1) ? n : n1;  // search the other run
+    while (a < b) {
+      int c = (a + b) >> 1;
+      bool before = (x < n1) ? (w.dv[c] < v) : (w.dv[c] <= v);
+      if (before) a = c + 1; else b = c;
+    }
+    w.perm[(x < n1) ? x + (a - n1) : (x - n1) + a] = x;
+  }
+  __syncthreads();
+  // positions whose z is not negligible, in order (chunk counts, then a scan)
+  const int chunk = (n + nt - 1) / nt, c0 = tid * chunk, c1 = min(n, c0 + chunk);
+  int cnt = 0;
+  for (int q = c0; q < c1; ++q) cnt += !(rho * fabs(w.zs[w.perm[q]]) <= tol);
+  scnt[tid] = cnt;
+  __syncthreads();
+  for (int o = 1; o < nt; o <<= 1) {
+    int v = tid >= o ? scnt[tid - o] : 0;
+    __syncthreads();
+    scnt[tid] += v;
+    __syncthreads();
+  }
+  const int nns = scnt[nt - 1];
+  for (int q = c0, o = scnt[tid] - cnt; q < c1; ++q)
+    if (!(rho * fabs(w.zs[w.perm[q]]) <= tol)) w.nsl[o++] = q;
+  __syncthreads();
+  // the rotation test of every adjacent pair, from the undeflated values
+  for (int m = 1 + tid; m < nns; m += nt) {
+    const int pj = w.perm[w.nsl[m - 1]], t = w.perm[w.nsl[m]];
+    double zs_ = w.zs[pj], zc = w.zs[t];
+    double tau = hypot(zc, zs_);
+    double c = zc / tau, sn = -zs_ / tau;
+    double tdiff = w.dv[t] - w.dv[pj];
+    w.prot[m] = fabs(tdiff * c * sn) <= tol;
+    w.ptau[m] = tau;
+    w.pc[m] = c;
+    w.ps[m] = sn;
+  }
+  __syncthreads();
+  if (tid != 0) return;
+  int k = 0, nd = 0, nr = 0, pj = -1, mi = -1;
+  bool prev_rot = false;
   for (int s = 0; s < n; ++s) {
     int t = w.perm[s];
     if (rho * fabs(w.zs[t]) <= tol) {
@@ -221,12 +266,24 @@ __global__ void __launch_bounds__(1024) k_prep(int lo, int mid, int hi, const do
       ++nd;
       continue;
     }
+    ++mi;
     if (pj < 0) { pj = t; continue; }
-    double zs_ = w.zs[pj], zc = w.zs[t];
-    double tau = hypot(zc, zs_);
-    double c = zc / tau, sn = -zs_ / tau;
-    double tdiff = w.dv[t] - w.dv[pj];
-    if (fabs(tdiff * c * sn) <= tol) {
+    double tau, c, sn;
+    bool rot;
+    if (prev_rot) {  // pj was rotated into: its z and d changed
+      double zs_ = w.zs[pj], zc = w.zs[t];
+      tau = hypot(zc, zs_);
+      c = zc / tau;
+      sn = -zs_ / tau;
+      double tdiff = w.dv[t] - w.dv[pj];
+      rot = fabs(tdiff * c * sn) <= tol;
+    } else {
+      tau = w.ptau[mi];
+      c = w.pc[mi];
+      sn = w.ps[mi];
+      rot = w.prot[mi] != 0;
+    }
+    if (rot) {
       w.zs[t] = tau;
       w.zs[pj] = 0.0;
       w.ra[nr] = pj; w.rb[nr] = t; w.rc[nr] = c; w.rs[nr] = sn; ++nr;
@@ -237,11 +294,11 @@ __global__ void __launch_bounds__(1024) k_prep(int lo, int mid, int hi, const do
       w.dfx[nd] = pj;
       w.dfv[nd] = t2;
       ++nd;
-      pj = t;
     } else {
       w.ndx[k] = pj; w.ndd[k] = w.dv[pj]; w.ndz[k] = w.zs[pj]; ++k;
-      pj = t;
     }
+    prev_rot = rot;
+    pj = t;
   }
   if (pj >= 0) { w.ndx[k] = pj; w.ndd[k] = w.dv[pj]; w.ndz[k] = w.zs[pj]; ++k; }
   // both lists ascending (they are nearly sorted already)
@@ -438,8 +495,10 @@ DcWs carve(char* base, int M, size_t* used) {
   w.D = takeD(m); w.dd = takeD(m); w.zs = takeD(m); w.dv = takeD(m); w.ndd = takeD(m); w.ndz = takeD(m);
   w.dfv = takeD(m); w.rc = takeD(m); w.rs = takeD(m); w.tauR = takeD(m); w.lam = takeD(m); w.zhat = takeD(m);
   w.newD = takeD(m); w.rho = takeD(4);
+  w.ptau = takeD(m); w.pc = takeD(m); w.ps = takeD(m);
   w.perm = takeI(m); w.ndx = takeI(m); w.dfx = takeI(m); w.ra = takeI(m); w.rb = takeI(m); w.org = takeI(m);
   w.posr = takeI(m); w.posd = takeI(m); w.cnt = takeI(8);
+  w.nsl = takeI(m); w.prot = takeI(m);
   *used = align256(off);
   return w;
 }

@@ -206,7 +206,7 @@ int dgemm_f64(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, 
   // A few output tiles with a long K leave most SMs idle: split K across CTAs.
   if (tiles < h->sm_count && k >= 1024 && h->d_splitk != nullptr) {
     long long nz = (2LL * h->sm_count + tiles - 1) / tiles;
-    nz = nz < k / 256 ? nz : k / 256;
+    nz = nz < k / 64 ? nz : k / 64;  // slices of at least 64: the FP64 pipe, not the loads, is the limit
     long long cap = (long long)(h->splitk_bytes / (sizeof(double) * (size_t)m * n));
     nz = nz < cap ? nz : cap;
     if (nz >= 2) {
