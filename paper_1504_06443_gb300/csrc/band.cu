@@ -168,8 +168,8 @@ __global__ void __launch_bounds__(PQ_ROWS) k_pqr_coop(int n, int nb, int rp, dou
                                                       double* __restrict__ tau, int* bar, int* st) {
   extern __shared__ double Ps[];  // [rp][nb + 1]
   __shared__ double sd[BMAX], sw[BMAX], sc[3];
-  __shared__ double prod[PQ_ROWS][PQ_CH + 1];
-  __shared__ double seg[PQ_ROWS / PQ_CH][PQ_CH];
+  __shared__ double pnv[PQ_ROWS];      // P(r, nc) of the rows below the next pivot, else 0
+  __shared__ double red4[4][BMAX];     // per-column partial dots of the four row quarters
   __shared__ int gok;
   if (status_bad(st)) return;
   const int t = threadIdx.x, G = gridDim.x, blk = blockIdx.x;
@@ -224,32 +224,24 @@ __global__ void __launch_bounds__(PQ_ROWS) k_pqr_coop(int n, int nb, int rp, dou
       for (int j = c + 1; j < nb; ++j) row[j] -= tk * vr * sw[j];
     }
     if (nc < nb) {
-      const double pn = (live && r > nc) ? row[nc] : 0.0;
-      for (int cb = nc; cb < nb; cb += PQ_CH) {
-        for (int q = 0; q < PQ_CH; ++q) {
-          int j = cb + q;
-          double pr = 0.0;
-          if (live && j < nb) {
-            if (r == nc) rout[j] = row[j];
-            if (r > nc) pr = pn * row[j];
-          }
-          if (mine) prod[t][q] = pr;
-        }
-        __syncthreads();
-        if (t < rp) {
-          int q = t % PQ_CH, sg = t / PQ_CH;
-          double sum = 0.0;
-          for (int i = 0; i < PQ_CH; ++i) sum += prod[sg * PQ_CH + i][q];
-          seg[sg][q] = sum;
-        }
-        __syncthreads();
-        if (t < PQ_CH && cb + t < nb) {
-          double sum = 0.0;
-          for (int sg = 0; sg < rp / PQ_CH; ++sg) sum += seg[sg][t];
-          pout[(size_t)(cb + t) * G + blk] = sum;
-        }
-        __syncthreads();
+      // partial dots of column nc with columns j >= nc over this CTA's rows below the pivot:
+      // thread (j = t mod 64, quarter t / 64) accumulates with FMAs down its rows, then the
+      // four quarters are added (the FP64 pipe, not the loads, bounds this phase)
+      if (mine) {
+        pnv[t] = (live && r > nc) ? row[nc] : 0.0;
+        if (live && r == nc)
+          for (int j = nc; j < nb; ++j) rout[j] = row[j];
       }
+      __syncthreads();
+      {
+        const int j = t & (BMAX - 1), qtr = t >> 6;
+        double sum = 0.0;
+        if (j >= nc && j < nb)
+          for (int i = qtr; i < rp; i += 4) sum = fma(pnv[i], Ps[i * ld + j], sum);
+        red4[qtr][j] = sum;
+      }
+      __syncthreads();
+      if (t >= nc && t < nb) pout[(size_t)t * G + blk] = (red4[0][t] + red4[1][t]) + (red4[2][t] + red4[3][t]);
     }
     if (c + 1 >= nref) break;  // the last step needs no exchange
     // grid barrier: this CTA's pout / rout are complete and visible before any CTA reads them
