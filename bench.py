@@ -544,7 +544,9 @@ def main():
                            "M": M, "seed": a.seed, "reducer": a.reducer, "sep": a.sep,
                            "bandwidth": (a.bandwidth or 64) if a.sep == "2stage" else None,
                            "precision": a.precision, "parallelism": "replicas" if world > 1 else "single",
-                           "l2": "inputs larger than L2 (8.6 GB per matrix at M=32768)",
+                           "l2": (f"inputs larger than L2 ({8.0 * M * M / 1e9:.2f} GB per matrix, L2 129 MB)"
+                                  if 8.0 * M * M > 129e6 else
+                                  f"inputs smaller than L2 ({8.0 * M * M / 1e6:.1f} MB per matrix), not flushed"),
                            "generator_s": round(gen_s, 2)},
                 "stage_ms": dict(zip(["R1_cholesky", "R2_reduce", "S1_tridiag", "S2_dc", "S3_back_q",
                                       "R3_backsub", "MP3_refine"], [round(x, 2) for x in stages])),
