@@ -206,6 +206,16 @@ int gep_batched_info(gep_handle_t h, int* info);
 int gep_get_info(gep_handle_t h, int* info);
 int gep_reset_info(gep_handle_t h);
 
+/* Failure-detection hook (tests).  Every device-side wait of the bulge chasing (S1c: step k
+ * of sweep s waits for step k+1 of sweep s-1) gives up after wait_limit_s seconds
+ * (0 < wait_limit_s <= 4; default 4), records GEP_ERR_TIMEOUT for gep_get_info and returns;
+ * the waits behind it see the error and return too, so the launch ends and the context stays
+ * usable.  drop_sweep >= 0 makes that sweep publish no progress (a message dropped on
+ * purpose, so that the next sweep's wait runs out); -1 (the default) injects nothing.
+ * Returns -2 / -3 for an out-of-range drop_sweep / wait_limit_s.  Clear the recorded error
+ * with gep_reset_info. */
+int gep_set_wait_fault(gep_handle_t h, int drop_sweep, double wait_limit_s);
+
 /* Per-stage times (ms) of the last gep_solve with o->timers = 1:
  * t[0] Cholesky (R1), t[1] reduction (R2), t[2] tridiagonalisation (TRD/BAND),
  * t[3] tridiagonal eigensolver (D&C), t[4] Householder back-transform (BACK),

@@ -28,6 +28,9 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libgep.so")
 RED_TWOSIDED, RED_EXPLICIT_INV = 0, 1
 SEP_1STAGE, SEP_2STAGE = 0, 1
 PREC_FP64, PREC_FP64_EMULATED, PREC_MIXED_REFINED = 0, 1, 2
+# return codes of include/gep.h
+ERR_CUDA, ERR_ALLOC, ERR_NONFINITE, ERR_TIMEOUT, ERR_HANDLE, ERR_UNSUPPORTED, ERR_TOO_LARGE = (
+    -100, -101, -102, -103, -104, -105, -106)
 
 _REDUCERS = {"twosided": RED_TWOSIDED, "explicit_inv": RED_EXPLICIT_INV}
 _SEPS = {"1stage": SEP_1STAGE, "2stage": SEP_2STAGE}
@@ -90,6 +93,7 @@ def load():
             "gep_solve_host": (_I, [_P, _I, _P, _I, _P, _I, _P, _P, _I, ctypes.POINTER(GepOptions)]),
             "gep_get_info": (_I, [_P, ctypes.POINTER(_I)]),
             "gep_reset_info": (_I, [_P]),
+            "gep_set_wait_fault": (_I, [_P, _I, _D]),
             "gep_get_stage_times": (_I, [_P, ctypes.POINTER(_D)]),
             "gep_launch_count": (ctypes.c_longlong, [_P, _I]),
             "gep_refine_steps": (_I, [_P]),
@@ -195,6 +199,12 @@ class Handle:
 
     def reset_info(self):
         _check(self.lib.gep_reset_info(self.h), "gep_reset_info")
+
+    def set_wait_fault(self, drop_sweep=-1, wait_limit_s=4.0):
+        """Failure-detection hook: bounded device waits give up after wait_limit_s seconds
+        (at most 4) with GEP_ERR_TIMEOUT; drop_sweep >= 0 stops that bulge-chasing sweep from
+        publishing progress, so the wait behind it runs out (-1: no injection)."""
+        _check(self.lib.gep_set_wait_fault(self.h, int(drop_sweep), float(wait_limit_s)), "gep_set_wait_fault")
 
     def stage_times(self):
         t = (_D * 7)()

@@ -210,6 +210,15 @@ int gep_reset_info(gep_handle_t h) {
   return reset_status(h);
 }
 
+int gep_set_wait_fault(gep_handle_t h, int drop_sweep, double wait_limit_s) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (drop_sweep < -1) return -2;
+  if (!(wait_limit_s > 0.0 && wait_limit_s <= 4.0)) return -3;
+  h->fault_drop_sweep = drop_sweep;
+  h->wait_limit_ns = (unsigned long long)(wait_limit_s * 1e9);
+  return GEP_OK;
+}
+
 long long gep_launch_count(gep_handle_t h, int reset) {
   if (!handle_ok(h)) return -1;
   long long n = h->launches;

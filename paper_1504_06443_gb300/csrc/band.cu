@@ -305,6 +305,8 @@ struct BulgeArgs {
   int* prog;          // prog[s] = steps of sweep s completed
   double* q2;         // diamond storage (or null)
   int* st;
+  unsigned long long wait_ns;  // limit of each progress wait
+  int drop_sweep;              // test hook: this sweep publishes no progress (-1: none)
 };
 
 // Diamond (j, k) base in the reflector storage: [V: 2b x b][tau: b][T: b x b].
@@ -475,7 +477,7 @@ __global__ void __launch_bounds__(256) k_bulge(BulgeArgs a) {
         unsigned long long t0 = gclock();
         while (ld_acquire(a.prog + (s - 1)) < need) {
           if (*(volatile int*)(a.st + 1) != 0) { abort_flag = 1; break; }
-          if (gclock() - t0 > 4000000000ull) {
+          if (gclock() - t0 > a.wait_ns) {
             atomicExch(a.st + 1, GEP_ERR_TIMEOUT);
             abort_flag = 1;
             break;
@@ -562,7 +564,7 @@ __global__ void __launch_bounds__(256) k_bulge(BulgeArgs a) {
       if (t < b) vp[t] = vc[t];
       taup = tk;
       __syncthreads();  // every thread's stores of this step precede the release below
-      if (t == 0) {
+      if (t == 0 && s != a.drop_sweep) {
         __threadfence();
         st_release(a.prog + s, k + 1);
       }
@@ -907,6 +909,8 @@ int band_to_tridiag(gep_handle_t h, int M, const double* C, int ldc, int b, doub
     if (grid > M - 1) grid = M - 1;
     BulgeArgs a;
     a.M = M; a.b = b; a.ldab = ldab; a.Q = Q; a.AB = AB; a.prog = prog; a.q2 = q2; a.st = h->d_status;
+    a.wait_ns = h->wait_limit_ns;
+    a.drop_sweep = h->fault_drop_sweep;
     void* args[] = {&a};
     GEP_CUDA(cudaLaunchCooperativeKernel((void*)k_bulge, dim3(grid), dim3(256), args, smem, h->stream));
     GEP_CHECK(check_launch(h));

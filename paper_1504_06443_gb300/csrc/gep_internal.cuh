@@ -19,6 +19,10 @@ struct gep_handle_s {
   size_t splitk_bytes = 0;
   long long launches = 0;
   int sm_count = 152;
+  // bounded device-side waits: their limit, and a test hook that drops the progress
+  // releases of one bulge-chasing sweep so that the waits behind it run out
+  unsigned long long wait_limit_ns = 4000000000ull;
+  int fault_drop_sweep = -1;
   int magic = 0x6e70;
   cudaEvent_t ev[8] = {};
   cudaEvent_t ev_band = nullptr;  // between full->band and bulge chasing (two-stage, timers on)
