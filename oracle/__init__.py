@@ -58,6 +58,8 @@ def _load():
             lib.oc_backsub.argtypes = [_I, _I, _D, _I, _D, _I]
             lib.oc_gep_solve.argtypes = [_I, _D, _I, _D, _I, _D, _D, _I, _I]
             lib.oc_gep_solve.restype = _I
+            lib.oc_gep_solve_eigenexa.argtypes = [_I, _D, _I, _D, _I, _D, _D, _I, _I]
+            lib.oc_gep_solve_eigenexa.restype = _I
             lib.oc_jacobi.argtypes = [_I, _D, _I, _D, _D, _I]
             lib.oc_jacobi.restype = _I
             lib.oc_inertia.argtypes = [_I, _D, _I, _D, _I, ctypes.c_double,
@@ -159,6 +161,18 @@ def gep_solve(A, B, want_vectors=True):
     Y = np.zeros((M, M), order="F") if want_vectors else None
     info = _load().oc_gep_solve(M, _p(Af), max(M, 1), _p(Bf), max(M, 1), _p(w), _p(Y), max(M, 1),
                                 1 if want_vectors else 0)
+    return w, Y, int(info)
+
+
+def gep_solve_eigenexa(A, B, want_vectors=True):
+    """Eq. 7-9 (Cholesky-free reducer): (w ascending, Y B-orthonormal or None, info)."""
+    Af = _colmajor(A)
+    Bf = _colmajor(B)
+    M = Af.shape[0]
+    w = np.zeros(M)
+    Y = np.zeros((M, M), order="F") if want_vectors else None
+    info = _load().oc_gep_solve_eigenexa(M, _p(Af), max(M, 1), _p(Bf), max(M, 1), _p(w), _p(Y), max(M, 1),
+                                         1 if want_vectors else 0)
     return w, Y, int(info)
 
 

@@ -17,6 +17,8 @@
  *           Sturm-sequence bisection (eigenvalue-only mode, T_evo)    oc_bisect
  *   Eq. 6   Y = U^-1 Z = L^-T Z                                      oc_backsub
  *   Eq. 2   full GEP driver, ascending order, sign convention       oc_gep_solve
+ *   Eq. 7-9 Cholesky-free reducer: SEP of B, A' = D^-1/2 W^T A W D^-1/2,
+ *           Y = W D^-1/2 Z                                          oc_gep_solve_eigenexa
  * Independent pins that do not reuse the pipeline above:
  *   cyclic Jacobi on a small symmetric matrix                       oc_jacobi
  *   Sylvester inertia of A - sigma B (Bunch-Parlett LDL^T)          oc_inertia
@@ -395,6 +397,89 @@ int oc_gep_solve(int M, const double* A, int lda, const double* B, int ldb, doub
   free(d);
   free(C);
   free(L);
+  return status ? M + status : 0;
+}
+
+/* ----------------------------------------------------------- Eq. 7 - 9 ---
+ * Cholesky-free ("EigenExa style") GEP solve, section 3.1:
+ *   B W = W D                       standard eigenproblem of B (Eq. 7),
+ *   A' = (D^-1/2 W^T) A (W D^-1/2)  reduced standard problem (Eq. 8),
+ *   A' Z = Z Lambda,  Y = W D^-1/2 Z (Eq. 9),
+ * each standard problem solved by the same TRD + QL route as oc_gep_solve.  Same
+ * arguments, outputs and conventions as oc_gep_solve; returns 0, n in 1..M when B has
+ * n eigenvalues <= 0 (B not positive definite), or M + l if QL failed. */
+int oc_gep_solve_eigenexa(int M, const double* A, int lda, const double* B, int ldb, double* w, double* Y,
+                          int ldy, int want_vectors) {
+  if (M <= 0) return 0;
+  size_t n2 = (size_t)M * M;
+  double* S = (double*)malloc(sizeof(double) * n2);
+  double* X = (double*)malloc(sizeof(double) * n2);
+  double* d = (double*)malloc(sizeof(double) * (size_t)M);
+  double* e = (double*)calloc((size_t)M, sizeof(double));
+  int status = 0;
+  /* Eq. 7: W (into X) and D (into d) */
+  for (int j = 0; j < M; ++j)
+    for (int i = 0; i < M; ++i) S[IX(i, j, M)] = B[IX(i, j, ldb)];
+  oc_tridiag(M, S, M, d, e, X, M);
+  status = oc_tql(M, d, e, X, M);
+  if (status) goto done;
+  {
+    int nonpos = 0;
+    for (int i = 0; i < M; ++i) nonpos += !(d[i] > 0.0);
+    if (nonpos) { status = -nonpos; goto done; }
+  }
+  /* X = W D^-1/2 */
+  for (int j = 0; j < M; ++j) {
+    double s = 1.0 / sqrt(d[j]);
+    for (int i = 0; i < M; ++i) X[IX(i, j, M)] *= s;
+  }
+  /* Eq. 8: A' = X^T (A X), A read through its lower triangle */
+  {
+    double* T = (double*)malloc(sizeof(double) * n2);
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < M; ++j)
+      for (int i = 0; i < M; ++i) {
+        double t = 0.0;
+        for (int k = 0; k < M; ++k) t += sym_lower(A, lda, i, k) * X[IX(k, j, M)];
+        T[IX(i, j, M)] = t;
+      }
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < M; ++j)
+      for (int i = 0; i < M; ++i) {
+        double t = 0.0;
+        for (int k = 0; k < M; ++k) t += X[IX(k, i, M)] * T[IX(k, j, M)];
+        S[IX(i, j, M)] = t;
+      }
+    free(T);
+  }
+  /* Eq. 9: A' Z = Z Lambda, Y = X Z */
+  for (int i = 0; i < M; ++i) e[i] = 0.0;
+  if (want_vectors && Y) {
+    double* Z = (double*)malloc(sizeof(double) * n2);
+    oc_tridiag(M, S, M, d, e, Z, M);
+    status = oc_tql(M, d, e, Z, M);
+    if (!status) {
+#pragma omp parallel for schedule(static)
+      for (int j = 0; j < M; ++j)
+        for (int i = 0; i < M; ++i) {
+          double t = 0.0;
+          for (int k = 0; k < M; ++k) t += X[IX(i, k, M)] * Z[IX(k, j, M)];
+          Y[IX(i, j, ldy)] = t;
+        }
+      for (int i = 0; i < M; ++i) w[i] = d[i];
+      sort_and_sign(M, w, Y, ldy);
+    }
+    free(Z);
+  } else {
+    oc_tridiag(M, S, M, d, e, NULL, 0);
+    oc_bisect(M, d, e, w);
+  }
+done:
+  free(e);
+  free(d);
+  free(X);
+  free(S);
+  if (status < 0) return -status;
   return status ? M + status : 0;
 }
 

@@ -323,3 +323,78 @@ def test_adjoint_central_differences(oracle_lib):
         fd = (loss(A + h * dA, B + h * dB) - loss(A - h * dA, B - h * dB)) / (2 * h)
         an = np.sum(Ab * dA) + np.sum(Bb * dB)
         assert abs(fd - an) <= 1e-5 * max(1.0, abs(fd)), (fd, an)
+
+
+# ------------------------------------------- Eq. 7-9 Cholesky-free reducer
+
+@pytest.mark.parametrize("M,seed", [(1, 0), (2, 1), (17, 2), (64, 3), (150, 4)])
+def test_eigenexa_known_spectrum(oracle_lib, M, seed):
+    """SEP of B, A' = D^-1/2 W^T A W D^-1/2, Y = W D^-1/2 Z: the planted spectrum and
+    B-orthonormal eigenvectors L0^-T Q (up to sign) come out, as with Eq. 4-6."""
+    g = gi.known_spectrum(M, seed)
+    w, Y, info = oracle_lib.gep_solve_eigenexa(g["A"], g["B"])
+    assert info == 0
+    lam = np.sort(g["lam"])
+    _check_gep(g["A"], g["B"], w, Y, lam_ref=lam)
+    Yx = np.linalg.solve(g["L0"].T, g["Q"])[:, np.argsort(g["lam"])]
+    idx = np.argmax(np.abs(Yx), axis=0)
+    Yx = Yx * np.sign(Yx[idx, np.arange(M)])[None, :]
+    if M > 1 and np.min(np.diff(lam)) > 1e-3:
+        assert np.max(np.abs(Y - Yx)) <= 1e-9
+
+
+def test_eigenexa_closed_forms_and_special_cases(oracle_lib):
+    with open(os.path.join(GOLDEN, "gep_closed_forms.json")) as f:
+        cases = json.load(f)["cases"]
+    for c in cases:
+        w, _, info = oracle_lib.gep_solve_eigenexa(np.array(c["A"]), np.array(c["B"]))
+        assert info == 0
+        assert np.max(np.abs(w - np.array(c["lambda"]))) <= 1e-14 * 8, c["name"]
+    # B = I: the standard problem (library eigensolver)
+    rng = np.random.default_rng(21)
+    G = rng.standard_normal((60, 60))
+    A = G + G.T
+    w, Y, info = oracle_lib.gep_solve_eigenexa(A, np.eye(60))
+    assert info == 0
+    assert np.max(np.abs(w - np.linalg.eigvalsh(A))) <= 1e-13 * _two_norm(A)
+    _check_gep(A, np.eye(60), w, Y)
+    # diagonal pencil: lambda_i = A_ii / B_ii
+    a = rng.standard_normal(25)
+    b = rng.uniform(0.5, 3.0, 25)
+    w, _, info = oracle_lib.gep_solve_eigenexa(np.diag(a), np.diag(b))
+    assert info == 0
+    assert np.max(np.abs(w - np.sort(a / b))) <= 8 * EPS * np.max(np.abs(a / b))
+
+
+def test_eigenexa_matches_cholesky_route_tight_binding(oracle_lib):
+    """The paper's reducers all solve the same GEP (Table 1): the Cholesky-free route agrees
+    with the Cholesky route (Eq. 4-6) and with scipy's generalized eigensolver."""
+    import scipy.linalg
+    tb = gi.tight_binding(128, seed=5)
+    A, B = tb["A"], tb["B"]
+    w1, Y1, i1 = oracle_lib.gep_solve(A, B)
+    w2, Y2, i2 = oracle_lib.gep_solve_eigenexa(A, B)
+    assert i1 == i2 == 0
+    nA = _two_norm(A)
+    assert np.max(np.abs(w1 - w2)) <= 1e-12 * nA
+    assert np.max(np.abs(w2 - scipy.linalg.eigh(A, B, eigvals_only=True))) <= 1e-12 * nA
+    _check_gep(A, B, w2, Y2)
+    iso = np.ones(128, dtype=bool)
+    gaps = np.diff(w1)
+    iso[1:] &= gaps > 1e-6 * nA
+    iso[:-1] &= gaps > 1e-6 * nA
+    assert np.max(np.abs(Y1[:, iso] - Y2[:, iso])) <= 1e-8
+    w3, _, i3 = oracle_lib.gep_solve_eigenexa(A, B, want_vectors=False)
+    assert i3 == 0 and np.max(np.abs(w3 - w2)) <= 1e-12 * nA
+
+
+def test_eigenexa_reports_indefinite_B(oracle_lib):
+    """B with two negative eigenvalues: no Cholesky here, the count of non-positive
+    eigenvalues of B is reported instead."""
+    rng = np.random.default_rng(22)
+    Q, _ = np.linalg.qr(rng.standard_normal((12, 12)))
+    dB = np.array([1.0, -0.5, 2.0, 3.0, -4.0, 1.5, 2.5, 0.7, 1.1, 1.9, 2.2, 3.3])
+    B = (Q * dB[None, :]) @ Q.T
+    B = 0.5 * (B + B.T)
+    _, _, info = oracle_lib.gep_solve_eigenexa(np.eye(12), B)
+    assert info == 2
