@@ -61,3 +61,24 @@ def test_null_handle_rejected_without_gpu(libpath):
     lib.gep_cholesky.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
     lib.gep_cholesky.restype = ctypes.c_int
     assert lib.gep_cholesky(None, 4, None, 4) == -104
+
+
+def test_host_checks_without_gpu(libpath):
+    """Calls that validate on the host answer without touching a device: a null handle is
+    GEP_ERR_HANDLE for the failure-detection hook and the status calls too."""
+    lib = ctypes.CDLL(libpath)
+    lib.gep_set_wait_fault.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
+    lib.gep_set_wait_fault.restype = ctypes.c_int
+    assert lib.gep_set_wait_fault(None, 0, 0.05) == -104
+    lib.gep_reset_info.argtypes = [ctypes.c_void_p]
+    lib.gep_reset_info.restype = ctypes.c_int
+    assert lib.gep_reset_info(None) == -104
+    lib.gep_get_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
+    lib.gep_get_info.restype = ctypes.c_int
+    v = ctypes.c_int(7)
+    assert lib.gep_get_info(None, ctypes.byref(v)) == -104
+    lib.sep_q2_elems.argtypes = [ctypes.c_int, ctypes.c_int]
+    lib.sep_q2_elems.restype = ctypes.c_size_t
+    assert lib.sep_q2_elems(100, 0) == 0 and lib.sep_q2_elems(1, 8) == 0
+    # (Q + 1)(Q + 2)/2 diamonds of 3b^2 + b doubles, Q = (M - 2) / b
+    assert lib.sep_q2_elems(100, 8) == (12 + 1) * (12 + 2) // 2 * (3 * 64 + 8)
