@@ -60,6 +60,8 @@ def _load():
             lib.oc_gep_solve.restype = _I
             lib.oc_gep_solve_eigenexa.argtypes = [_I, _D, _I, _D, _I, _D, _D, _I, _I]
             lib.oc_gep_solve_eigenexa.restype = _I
+            lib.oc_gep_solve_partial.argtypes = [_I, _D, _I, _D, _I, _I, _D, _D, _I]
+            lib.oc_gep_solve_partial.restype = _I
             lib.oc_jacobi.argtypes = [_I, _D, _I, _D, _D, _I]
             lib.oc_jacobi.restype = _I
             lib.oc_inertia.argtypes = [_I, _D, _I, _D, _I, ctypes.c_double,
@@ -174,6 +176,18 @@ def gep_solve_eigenexa(A, B, want_vectors=True):
     info = _load().oc_gep_solve_eigenexa(M, _p(Af), max(M, 1), _p(Bf), max(M, 1), _p(w), _p(Y), max(M, 1),
                                          1 if want_vectors else 0)
     return w, Y, int(info)
+
+
+def gep_solve_partial(A, B, n_want):
+    """The n_want lowest eigenpairs (bisection + inverse iteration): (w, Y M x n_want, info)."""
+    Af = _colmajor(A)
+    Bf = _colmajor(B)
+    M = Af.shape[0]
+    n = max(0, min(int(n_want), M))
+    w = np.zeros(max(n, 1))
+    Y = np.zeros((M, max(n, 1)), order="F")
+    info = _load().oc_gep_solve_partial(M, _p(Af), max(M, 1), _p(Bf), max(M, 1), n, _p(w), _p(Y), max(M, 1))
+    return w[:n], Y[:, :n], int(info)
 
 
 def jacobi(S, want_v=True):

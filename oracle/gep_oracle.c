@@ -19,6 +19,7 @@
  *   Eq. 2   full GEP driver, ascending order, sign convention       oc_gep_solve
  *   Eq. 7-9 Cholesky-free reducer: SEP of B, A' = D^-1/2 W^T A W D^-1/2,
  *           Y = W D^-1/2 Z                                          oc_gep_solve_eigenexa
+ *   lowest n eigenpairs: bisection + inverse iteration on T          oc_gep_solve_partial
  * Independent pins that do not reuse the pipeline above:
  *   cyclic Jacobi on a small symmetric matrix                       oc_jacobi
  *   Sylvester inertia of A - sigma B (Bunch-Parlett LDL^T)          oc_inertia
@@ -274,11 +275,11 @@ int oc_sturm_count(int M, const double* d, const double* e, double sigma) {
   return cnt;
 }
 
-/* Eigenvalues of the tridiagonal (d, e) in ascending order by bisection on
- * the Sturm count, each bracketed until the interval no longer shrinks
- * (width at the level of one ulp).  Independent of oc_tql. */
-void oc_bisect(int M, const double* d, const double* e, double* w) {
-  if (M <= 0) return;
+/* Eigenvalues k0 .. k1-1 (ascending order) of the tridiagonal (d, e) into
+ * w[0 .. k1-k0) by bisection on the Sturm count, each bracketed until the interval
+ * no longer shrinks (width at the level of one ulp).  Independent of oc_tql. */
+static void bisect_range(int M, const double* d, const double* e, int k0, int k1, double* w) {
+  if (M <= 0 || k1 <= k0) return;
   double lo = d[0], hi = d[0];
   for (int i = 0; i < M; ++i) {
     double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < M ? fabs(e[i]) : 0.0);
@@ -289,7 +290,7 @@ void oc_bisect(int M, const double* d, const double* e, double* w) {
   lo -= 1e-12 * span + 1e-300;
   hi += 1e-12 * span + 1e-300;
 #pragma omp parallel for schedule(dynamic, 8)
-  for (int k = 0; k < M; ++k) {
+  for (int k = k0; k < k1; ++k) {
     /* smallest x with count(x) > k: the (k+1)-th eigenvalue */
     double a = lo, b = hi;
     for (int it = 0; it < 200; ++it) {
@@ -297,9 +298,12 @@ void oc_bisect(int M, const double* d, const double* e, double* w) {
       if (mid <= a || mid >= b) break;
       if (oc_sturm_count(M, d, e, mid) > k) b = mid; else a = mid;
     }
-    w[k] = 0.5 * (a + b);
+    w[k - k0] = 0.5 * (a + b);
   }
 }
+
+/* All M eigenvalues of (d, e), ascending. */
+void oc_bisect(int M, const double* d, const double* e, double* w) { bisect_range(M, d, e, 0, M, w); }
 
 /* ---------------------------------------------------------------- Eq. 6 ---
  * Back-transformation Y = L^-T Z: back substitution with the upper triangular
@@ -481,6 +485,145 @@ done:
   free(S);
   if (status < 0) return -status;
   return status ? M + status : 0;
+}
+
+/* ------------------------------------------------------ partial spectrum ---
+ * The n_want lowest eigenpairs only (the occupied states of the electronic-structure
+ * use case): Cholesky (Eq. 4), reduction (Eq. 5), tridiagonalisation with explicit Q,
+ * Sturm bisection for eigenvalues 0 .. n_want-1, inverse iteration on T for their
+ * vectors (Golub & Van Loan, inverse iteration: LU with partial pivoting of T - sigma I,
+ * a fixed number of solves from a deterministic start; vectors whose eigenvalues lie
+ * within 1e-3 ||T|| of the previous one form a cluster and are re-orthogonalised against
+ * its earlier members; shifts of equal eigenvalues are separated by 10 eps ||T||),
+ * Z = Q X and Y = L^-T Z (Eq. 6).  w[n_want] ascending; Y (M x n_want, ldy) B-orthonormal
+ * with the sign convention of sort_and_sign.  Returns 0 or k in 1..M as oc_gep_solve. */
+
+/* x <- (T - sigma I)^-1 x using the factors of tri_lu. */
+static void tri_solve(int n, const double* u0, const double* u1, const double* u2, const double* l,
+                      const int* piv, double* x) {
+  for (int i = 0; i + 1 < n; ++i) {
+    if (piv[i]) { double t = x[i]; x[i] = x[i + 1]; x[i + 1] = t; }
+    x[i + 1] -= l[i] * x[i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double t = x[i];
+    if (i + 1 < n) t -= u1[i] * x[i + 1];
+    if (i + 2 < n) t -= u2[i] * x[i + 2];
+    x[i] = t / u0[i];
+  }
+}
+
+/* Gaussian elimination with partial pivoting of the tridiagonal T - sigma I: row i of U
+ * is (u0, u1, u2) on columns i, i+1, i+2; l[i], piv[i] record step i.  A zero pivot is
+ * replaced by tiny (the shift is an eigenvalue to working accuracy). */
+static void tri_lu(int n, const double* d, const double* e, double sigma, double tiny, double* u0,
+                   double* u1, double* u2, double* l, int* piv) {
+  double c0 = d[0] - sigma, c1 = (n > 1) ? e[0] : 0.0, c2 = 0.0;  /* current row */
+  for (int i = 0; i + 1 < n; ++i) {
+    double s0 = e[i], s1 = d[i + 1] - sigma, s2 = (i + 2 < n) ? e[i + 1] : 0.0;  /* next row */
+    if (fabs(c0) >= fabs(s0)) {
+      if (c0 == 0.0) c0 = tiny;
+      double m = s0 / c0;
+      u0[i] = c0; u1[i] = c1; u2[i] = c2; l[i] = m; piv[i] = 0;
+      c0 = s1 - m * c1;
+      c1 = s2 - m * c2;
+    } else {
+      double m = c0 / s0;
+      u0[i] = s0; u1[i] = s1; u2[i] = s2; l[i] = m; piv[i] = 1;
+      c0 = c1 - m * s1;
+      c1 = c2 - m * s2;
+    }
+    c2 = 0.0;
+  }
+  if (c0 == 0.0) c0 = tiny;
+  u0[n - 1] = c0;
+}
+
+int oc_gep_solve_partial(int M, const double* A, int lda, const double* B, int ldb, int n_want, double* w,
+                         double* Y, int ldy) {
+  if (M <= 0 || n_want <= 0) return 0;
+  if (n_want > M) n_want = M;
+  size_t n2 = (size_t)M * M;
+  double* L = (double*)malloc(sizeof(double) * n2);
+  double* C = (double*)malloc(sizeof(double) * n2);
+  for (int j = 0; j < M; ++j)
+    for (int i = 0; i < M; ++i) {
+      L[IX(i, j, M)] = B[IX(i, j, ldb)];
+      C[IX(i, j, M)] = A[IX(i, j, lda)];
+    }
+  int info = oc_cholesky(M, L, M);
+  if (info) { free(C); free(L); return info; }
+  oc_two_sided(M, C, M, L, M);
+  double* Q = (double*)malloc(sizeof(double) * n2);
+  double* d = (double*)malloc(sizeof(double) * (size_t)M);
+  double* e = (double*)calloc((size_t)M, sizeof(double));
+  oc_tridiag(M, C, M, d, e, Q, M);
+  bisect_range(M, d, e, 0, n_want, w);
+  double tnorm = 0.0;
+  for (int i = 0; i < M; ++i) {
+    double r = fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < M ? fabs(e[i]) : 0.0);
+    if (r > tnorm) tnorm = r;
+  }
+  if (tnorm == 0.0) tnorm = 1.0;
+  const double eps = 0x1p-53, sep = 10.0 * eps * tnorm, ortol = 1e-3 * tnorm;
+  double* X = (double*)calloc((size_t)M * n_want, sizeof(double));
+  double *u0 = (double*)malloc(sizeof(double) * M), *u1 = (double*)malloc(sizeof(double) * M);
+  double *u2 = (double*)malloc(sizeof(double) * M), *lm = (double*)malloc(sizeof(double) * M);
+  int* piv = (int*)malloc(sizeof(int) * (size_t)M);
+  int cl0 = 0;               /* first index of the current cluster */
+  double prev_shift = 0.0;
+  for (int j = 0; j < n_want; ++j) {
+    double sigma = w[j];
+    if (j > 0 && w[j] - w[j - 1] > ortol) cl0 = j;
+    if (j > cl0 && sigma - prev_shift < sep) sigma = prev_shift + sep;
+    prev_shift = sigma;
+    tri_lu(M, d, e, sigma, eps * tnorm, u0, u1, u2, lm, piv);
+    double* x = X + (size_t)j * M;
+    unsigned long long st = 0x9E3779B97F4A7C15ull * (unsigned long long)(j + 1);
+    for (int i = 0; i < M; ++i) {  /* deterministic start in [-1, 1] (splitmix64) */
+      st += 0x9E3779B97F4A7C15ull;
+      unsigned long long z = st;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      x[i] = (double)(z >> 11) * 0x1p-52 - 1.0;
+    }
+    for (int it = 0; it < 4; ++it) {
+      tri_solve(M, u0, u1, u2, lm, piv, x);
+      for (int k = cl0; k < j; ++k) {  /* re-orthogonalise within the cluster */
+        const double* y = X + (size_t)k * M;
+        double dot = 0.0;
+        for (int i = 0; i < M; ++i) dot += y[i] * x[i];
+        for (int i = 0; i < M; ++i) x[i] -= dot * y[i];
+      }
+      double nrm = 0.0;
+      for (int i = 0; i < M; ++i) nrm += x[i] * x[i];
+      nrm = sqrt(nrm);
+      for (int i = 0; i < M; ++i) x[i] /= nrm;
+    }
+  }
+  /* Z = Q X, then Y = L^-T Z */
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < n_want; ++j)
+    for (int i = 0; i < M; ++i) {
+      double t = 0.0;
+      for (int k = 0; k < M; ++k) t += Q[IX(i, k, M)] * X[IX(k, j, M)];
+      Y[IX(i, j, ldy)] = t;
+    }
+  oc_backsub(M, n_want, L, M, Y, ldy);
+  for (int j = 0; j < n_want; ++j) {  /* largest-magnitude entry positive, lowest row on ties */
+    int im = 0;
+    double best = -1.0;
+    for (int i = 0; i < M; ++i) {
+      double a = fabs(Y[IX(i, j, ldy)]);
+      if (a > best) { best = a; im = i; }
+    }
+    if (Y[IX(im, j, ldy)] < 0.0)
+      for (int i = 0; i < M; ++i) Y[IX(i, j, ldy)] = -Y[IX(i, j, ldy)];
+  }
+  free(piv); free(lm); free(u2); free(u1); free(u0); free(X);
+  free(e); free(d); free(Q); free(C); free(L);
+  return 0;
 }
 
 /* ---------------------------------------------- independent pin: Jacobi ---

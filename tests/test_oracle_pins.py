@@ -398,3 +398,58 @@ def test_eigenexa_reports_indefinite_B(oracle_lib):
     B = 0.5 * (B + B.T)
     _, _, info = oracle_lib.gep_solve_eigenexa(np.eye(12), B)
     assert info == 2
+
+
+# --------------------------------- lowest eigenpairs: bisection + inverse iteration
+
+@pytest.mark.parametrize("M,n", [(1, 1), (40, 13), (129, 64), (200, 200)])
+def test_partial_spectrum_matches_full_solve(oracle_lib, M, n):
+    """Inverse iteration on T shares no step with QL: its lowest n eigenpairs agree with the
+    full solve's first n (eigenvectors column by column where isolated)."""
+    tb = gi.tight_binding(M, seed=M) if M % 4 == 0 else gi.known_spectrum(M, seed=M)
+    A, B = tb["A"], tb["B"]
+    w, Y, info = oracle_lib.gep_solve(A, B)
+    wp, Yp, ip = oracle_lib.gep_solve_partial(A, B, n)
+    assert info == ip == 0 and wp.shape == (n,) and Yp.shape == (M, n)
+    nA = _two_norm(A)
+    assert np.max(np.abs(wp - w[:n])) <= 1e-12 * nA
+    res = np.linalg.norm(A @ Yp - (B @ Yp) * wp[None, :]) / (np.linalg.norm(A) * M)
+    assert res <= 1e-13, res
+    assert np.max(np.abs(Yp.T @ B @ Yp - np.eye(n))) <= 1e-12
+    gaps = np.diff(w)
+    iso = np.ones(M, dtype=bool)
+    iso[1:] &= gaps > 1e-6 * nA
+    iso[:-1] &= gaps > 1e-6 * nA
+    iso = iso[:n]
+    assert np.max(np.abs(Yp[:, iso] - Y[:, :n][:, iso]), initial=0.0) <= 1e-8
+
+
+def test_partial_spectrum_known_and_clustered(oracle_lib):
+    g = gi.known_spectrum(90, seed=6)
+    w, Y, info = oracle_lib.gep_solve_partial(g["A"], g["B"], 30)
+    assert info == 0
+    assert np.max(np.abs(w - np.sort(g["lam"])[:30])) <= 1e-11 * 20
+    # exactly repeated and 1e-9-spaced eigenvalues: the cluster's vectors stay B-orthonormal
+    c = gi.clustered_spectrum(120, seed=7)
+    w, Y, info = oracle_lib.gep_solve_partial(c["A"], c["B"], 60)
+    assert info == 0
+    assert np.max(np.abs(w - np.sort(c["lam"])[:60])) <= 1e-11 * 20
+    assert np.max(np.abs(Y.T @ c["B"] @ Y - np.eye(60))) <= 1e-12
+    res = np.linalg.norm(c["A"] @ Y - (c["B"] @ Y) * w[None, :]) / (np.linalg.norm(c["A"]) * 120)
+    assert res <= 1e-13, res
+
+
+def test_partial_spectrum_standard_problem_and_edges(oracle_lib):
+    rng = np.random.default_rng(31)
+    G = rng.standard_normal((70, 70))
+    A = G + G.T
+    w, Y, info = oracle_lib.gep_solve_partial(A, np.eye(70), 20)
+    assert info == 0
+    assert np.max(np.abs(w - np.linalg.eigvalsh(A)[:20])) <= 1e-13 * _two_norm(A)
+    w0, Y0, i0 = oracle_lib.gep_solve_partial(A, np.eye(70), 0)
+    assert i0 == 0 and w0.shape == (0,) and Y0.shape == (70, 0)
+    # B not positive definite: the Cholesky failure index, as in the full solve
+    Bbad = np.eye(70)
+    Bbad[5, 5] = -1.0
+    _, _, ib = oracle_lib.gep_solve_partial(A, Bbad, 10)
+    assert ib == 6
