@@ -157,6 +157,57 @@ def _sym_ptr_ld(t):
     raise ValueError("symmetric matrix argument must have a unit stride in one dimension")
 
 
+def _need_cuda(t, name):
+    if not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor (the library has no CPU path), got {t.device}")
+
+
+def _need_matrix(t, name, rows=None, cols=None, square=False, f64=False, cuda=True):
+    """Host-side check of a matrix argument before any pointer reaches the device: a 2-D CUDA
+    tensor of the stated size (float64 where the library reads the caller's buffer in place)."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch.Tensor, got {type(t).__name__}")
+    if t.dim() != 2:
+        raise ValueError(f"{name}: expected a 2-D tensor, got shape {tuple(t.shape)}")
+    if square and t.shape[0] != t.shape[1]:
+        raise ValueError(f"{name}: expected a square matrix, got shape {tuple(t.shape)}")
+    if rows is not None and t.shape[0] != rows:
+        raise ValueError(f"{name}: expected {rows} rows, got shape {tuple(t.shape)}")
+    if cols is not None and t.shape[1] != cols:
+        raise ValueError(f"{name}: expected {cols} columns, got shape {tuple(t.shape)}")
+    if f64 and t.dtype != torch.float64:
+        raise TypeError(f"{name}: expected float64, got {t.dtype}")
+    if cuda:
+        _need_cuda(t, name)
+
+
+def _need_vector(t, name, min_len, f64=False, cuda=True):
+    """Host-side check of a vector argument: a CUDA tensor with at least min_len elements."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch.Tensor, got {type(t).__name__}")
+    if t.numel() < min_len:
+        raise ValueError(f"{name}: expected at least {min_len} elements, got {t.numel()}")
+    if f64 and t.dtype != torch.float64:
+        raise TypeError(f"{name}: expected float64, got {t.dtype}")
+    if cuda:
+        _need_cuda(t, name)
+
+
+def _need_on_device(*named):
+    """Device check of already shape-checked arguments (pairs name, tensor; None skipped)."""
+    for name, t in zip(named[0::2], named[1::2]):
+        if t is not None:
+            _need_cuda(t, name)
+
+
+def _same_device(h, *ts):
+    for t in ts:
+        if t is not None and t.device != h.device:
+            raise ValueError(f"tensor on {t.device} but the handle is bound to {h.device}")
+
+
 class Handle:
     """A libgep handle bound to one CUDA stream, with a torch-allocated workspace."""
 
@@ -288,8 +339,18 @@ def solve(A, B, reducer="twosided", sep="1stage", precision="fp64", want_vectors
     Returns (w, Y, info): w ascending, Y (column-major view) B-orthonormal or None.
     info != 0 reports a numerical failure (k: B's leading minor k not positive definite)."""
     torch = _torch()
-    h = handle or default_handle()
+    _need_matrix(A, "A", square=True, f64=True, cuda=False)
     M = int(A.shape[0])
+    _need_matrix(B, "B", rows=M, cols=M, f64=True, cuda=False)
+    if out is not None:
+        _need_vector(out[0], "out[0] (w)", M, f64=True)
+        if want_vectors:
+            _need_matrix(out[1], "out[1] (Y^T)", rows=M, cols=M, f64=True)
+            if not out[1].is_contiguous():
+                raise ValueError("out[1] (Y^T) must be contiguous")
+    _need_on_device("A", A, "B", B)
+    h = handle or default_handle()
+    _same_device(h, A, B)
     o = make_options(reducer, sep, precision, want_vectors, overwrite, timers, bandwidth, refine_iters)
     n = _SZ()
     _check(h.lib.gep_workspace_size(h.h, M, ctypes.byref(o), ctypes.byref(n)), "gep_workspace_size")
@@ -308,6 +369,12 @@ def solve(A, B, reducer="twosided", sep="1stage", precision="fp64", want_vectors
 
 def solve_async(A, B, w, Yt, opts, handle):
     """Enqueue-only variant used by the benchmark: no synchronisation, no allocation."""
+    _need_matrix(A, "A", square=True, f64=True, cuda=False)
+    _need_matrix(B, "B", rows=A.shape[0], cols=A.shape[0], f64=True, cuda=False)
+    _need_vector(w, "w", A.shape[0], f64=True, cuda=False)
+    if Yt is not None:
+        _need_matrix(Yt, "Yt", rows=A.shape[0], cols=A.shape[0], f64=True, cuda=False)
+    _need_on_device("A", A, "B", B, "w", w, "Yt", Yt)
     pa, lda = _sym_ptr_ld(A)
     pb, ldb = _sym_ptr_ld(B)
     _check(handle.lib.gep_solve(handle.h, int(A.shape[0]), pa, lda, pb, ldb, _ptr(w), _ptr(Yt), max(1, A.shape[0]),
@@ -337,6 +404,7 @@ def solve_host(A_np, B_np, want_vectors=True, handle=None, **opts):
 
 def cholesky(B, handle=None):
     """Eq. 4: returns (L column-major, info)."""
+    _need_matrix(B, "B", square=True)
     h = handle or default_handle()
     L = colmajor(B.clone())
     M = L.shape[0]
@@ -357,6 +425,9 @@ def _stage_ws(M, ncol=None, handle=None):
 
 def reduce(A, L, variant="twosided", handle=None):
     """Eq. 5: (C, L_or_R).  For 'explicit_inv' the returned second matrix is R = L^-1."""
+    _need_matrix(A, "A", square=True, cuda=False)
+    _need_matrix(L, "L", rows=A.shape[0], cols=A.shape[0], cuda=False)
+    _need_on_device("A", A, "L", L)
     h = handle or default_handle()
     C = colmajor(A.clone())
     Lc = colmajor(L.clone())
@@ -368,6 +439,9 @@ def reduce(A, L, variant="twosided", handle=None):
 
 def gep_backtransform(LR, Z, variant="twosided", handle=None):
     """Eq. 6: Y = L^-T Z (twosided) or Y = R^T Z (explicit_inv)."""
+    _need_matrix(LR, "LR", square=True, cuda=False)
+    _need_matrix(Z, "Z", rows=LR.shape[0], cuda=False)
+    _need_on_device("LR", LR, "Z", Z)
     h = handle or default_handle()
     Y = colmajor(Z.clone())
     Lc = colmajor(LR)
@@ -381,6 +455,7 @@ def gep_backtransform(LR, Z, variant="twosided", handle=None):
 def tridiag_1stage(C, handle=None):
     """Householder tridiagonalisation: (d, e, tau, C_with_reflectors)."""
     torch = _torch()
+    _need_matrix(C, "C", square=True)
     h = handle or default_handle()
     Cc = colmajor(C.clone())
     M = Cc.shape[0]
@@ -395,8 +470,11 @@ def tridiag_1stage(C, handle=None):
 def tridiag_eig(d, e, want_vectors=True, handle=None):
     """Divide and conquer (or bisection when want_vectors=False): (w ascending, Z or None, info)."""
     torch = _torch()
-    h = handle or default_handle()
+    _need_vector(d, "d", 0, cuda=False)
     M = int(d.shape[0])
+    _need_vector(e, "e", max(M - 1, 0), cuda=False)
+    _need_on_device("d", d, "e", e)
+    h = handle or default_handle()
     dd = d.to(torch.float64).contiguous()
     ee = torch.zeros(max(M, 1), dtype=torch.float64, device=d.device)
     if M > 1:
@@ -413,6 +491,10 @@ def tridiag_eig(d, e, want_vectors=True, handle=None):
 def sep_backtransform(C_refl, tau, Z, handle=None):
     """Z <- Q Z with the reflectors of tridiag_1stage."""
     torch = _torch()
+    _need_matrix(C_refl, "C_refl", square=True, cuda=False)
+    _need_matrix(Z, "Z", rows=C_refl.shape[0], cuda=False)
+    _need_vector(tau, "tau", max(C_refl.shape[0] - 1, 0), cuda=False)
+    _need_on_device("C_refl", C_refl, "Z", Z, "tau", tau)
     h = handle or default_handle()
     Y = colmajor(Z.clone())
     Cc = colmajor(C_refl)
@@ -436,6 +518,7 @@ def tridiag_2stage(C, b=64, want_q2=True, handle=None):
     """Two-stage reduction (full -> band of width b -> tridiagonal):
     (d, e, tau1, q2 or None, C with the band and the panel reflectors)."""
     torch = _torch()
+    _need_matrix(C, "C", square=True)
     h = handle or default_handle()
     Cc = colmajor(C.clone())
     M = Cc.shape[0]
@@ -452,6 +535,13 @@ def tridiag_2stage(C, b=64, want_q2=True, handle=None):
 
 def sep_backtransform_2stage(C_refl, tau1, q2, b, Z, handle=None):
     """Z <- Q1 (Q2 Z) with the output of tridiag_2stage."""
+    _need_matrix(C_refl, "C_refl", square=True, cuda=False)
+    M = int(C_refl.shape[0])
+    _need_matrix(Z, "Z", rows=M, cuda=False)
+    _need_vector(tau1, "tau1", M, f64=True, cuda=False)
+    if M > 2:
+        _need_vector(q2, "q2", int(load().sep_q2_elems(M, int(b))), f64=True, cuda=False)
+    _need_on_device("C_refl", C_refl, "Z", Z, "tau1", tau1, "q2", q2)
     h = handle or default_handle()
     Y = colmajor(Z.clone())
     Cc = colmajor(C_refl)
@@ -463,13 +553,25 @@ def sep_backtransform_2stage(C_refl, tau1, q2, b, Z, handle=None):
 
 
 def dgemm(A, B, transa="N", transb="N", alpha=1.0, beta=0.0, C=None, uplo="F", engine="fp64", handle=None):
-    """C = alpha op(A) op(B) + beta C on the library's GEMM engine (column-major views)."""
+    """C = alpha op(A) op(B) + beta C on the library's GEMM engine (column-major views).
+    transa 'S': A symmetric with only its lower triangle read (op(A) = A)."""
     torch = _torch()
+    if transa not in ("N", "T", "S") or transb not in ("N", "T") or uplo not in ("F", "L"):
+        raise ValueError("transa in N/T/S, transb in N/T, uplo in F/L")
+    _need_matrix(A, "A", square=(transa == "S"), cuda=False)
+    _need_matrix(B, "B", cuda=False)
+    m = A.shape[1] if transa == "T" else A.shape[0]
+    k = A.shape[0] if transa == "T" else A.shape[1]
+    kb = B.shape[1] if transb == "T" else B.shape[0]
+    n = B.shape[0] if transb == "T" else B.shape[1]
+    if kb != k:
+        raise ValueError(f"inner dimensions differ: op(A) is {m} x {k}, op(B) is {kb} x {n}")
+    if C is not None:
+        _need_matrix(C, "C", rows=m, cols=n)
+    _need_cuda(A, "A")
+    _need_cuda(B, "B")
     h = handle or default_handle()
     Ac, Bc = colmajor(A), colmajor(B)
-    m = Ac.shape[1] if transa == "T" else Ac.shape[0]
-    k = Ac.shape[0] if transa == "T" else Ac.shape[1]
-    n = Bc.shape[0] if transb == "T" else Bc.shape[1]
     Cc = colmajor(C.clone()) if C is not None else torch.zeros((n, m), dtype=torch.float64, device=A.device).t()
     kp = min(max(k, 1), 4096)
     h.ensure_workspace(8 * (m + n) * (kp + 32) * 2 + 4 * (m + n) + 8192)
@@ -486,8 +588,17 @@ def adjoint(w, Y, n_occ, lbar=None, W=None, handle=None):
     w: eigenvalues ascending, Y: B-orthonormal eigenvectors (both from solve);
     lbar: M weights (None = 1 on the n_occ occupied, 0 elsewhere); W: symmetric or None."""
     torch = _torch()
-    h = handle or default_handle()
+    _need_vector(w, "w", 0, cuda=False)
     M = int(w.shape[0])
+    _need_matrix(Y, "Y", rows=M, cols=M, cuda=False)
+    if not 0 <= int(n_occ) <= M:
+        raise ValueError(f"n_occ must lie in [0, {M}]")
+    if lbar is not None:
+        _need_vector(lbar, "lbar", M, cuda=False)
+    if W is not None:
+        _need_matrix(W, "W", rows=M, cols=M, cuda=False)
+    _need_on_device("w", w, "Y", Y, "lbar", lbar, "W", W)
+    h = handle or default_handle()
     Yc = colmajor(Y)
     ww = w.to(torch.float64).contiguous()
     lb = None if lbar is None else lbar.to(torch.float64).contiguous()
@@ -613,6 +724,12 @@ class BatchedSolver:
 
     def __init__(self, As, Bs, nstreams=8, precision="fp64_emulated", precisions=None, handle=None):
         torch = _torch()
+        if len(As) != len(Bs) or len(As) == 0:
+            raise ValueError("As and Bs must be non-empty lists of the same length")
+        for i, (a, b) in enumerate(zip(As, Bs)):
+            _need_matrix(a, f"As[{i}]", square=True, f64=True, cuda=False)
+            _need_matrix(b, f"Bs[{i}]", rows=a.shape[0], cols=a.shape[0], f64=True, cuda=False)
+            _need_on_device(f"As[{i}]", a, f"Bs[{i}]", b)
         self.h = handle or Handle()
         self.count = len(As)
         self.As = [a.contiguous() for a in As]
