@@ -17,9 +17,10 @@
 // accumulators per output (levels 2..4 and 5..LMAX); FP64 arithmetic appears only
 // once per output element, in the final epilogue.
 //
-// Kernel: one 128 x 64 output tile per CTA, 10 warps: warp 0 issues TMA loads of
-// all S digit planes of a 32-deep K step (3-D boxes, 64-byte swizzle) into a
-// two-stage ring; warp 1 issues tcgen05.mma (M=128, K=16, N up to 256 covering
+// Kernel: persistent, grid = min(output tiles, SMs); each CTA walks 128 x 64 output
+// tiles (its TMA ring and barrier phases continue from one tile to the next), 10 warps:
+// warp 0 issues TMA loads of all S digit planes of a 32-deep K step (3-D boxes, 64-byte
+// swizzle) into a two-stage ring; warp 1 issues tcgen05.mma (M=128, K=16, N up to 256 covering
 // several levels at once: for fixed s the planes B_1..B_{LMAX-s} are contiguous in
 // shared memory and their levels are contiguous TMEM columns); warps 2-9 drain
 // TMEM (warp w reads lane quarter w%4, column half (w-2)/4).  Every mbarrier wait
