@@ -157,11 +157,12 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 
 // The whole panel QR in one cooperative launch: CTA g keeps panel rows [rp g, rp g + rp)
 // (rp = 64, 128 or 256: the per-SM FP64 rate bounds a step, so short panels take more
-// CTAs of fewer rows) in shared memory for all column steps, which follow k_pqr_step's
-// arithmetic; the
-// partial dot products and the next pivot row go through part/prow (ping-pong) across a
-// grid barrier.  bar[0] counts barrier arrivals (zero on entry); a barrier that does not
-// complete within 4 s records GEP_ERR_TIMEOUT and the CTA returns.
+// CTAs of fewer rows) in shared memory for all column steps.  Each step is k_pqr_step's
+// Householder step; the partial dot products of the next step are accumulated per column
+// with FMAs down the CTA's rows (four row quarters, then three adds).  The partial sums and
+// the next pivot row go through part/prow (ping-pong) across a grid barrier.  bar[0]
+// counts barrier arrivals (zero on entry); a barrier that does not complete within 4 s
+// records GEP_ERR_TIMEOUT and the CTA returns.
 __global__ void __launch_bounds__(PQ_ROWS) k_pqr_coop(int n, int nb, int rp, double* __restrict__ P, int ldp,
                                                       double* __restrict__ part0, double* __restrict__ part1,
                                                       double* __restrict__ prow0, double* __restrict__ prow1,
