@@ -59,3 +59,25 @@ def test_shard_batch_single_rank_and_ties():
     # equal orders alternate over ranks in index order, lower rank first
     assert shard_batch([100, 100, 100, 100], 2) == [[0, 2], [1, 3]]
     assert shard_batch([], 3) == [[], [], []]
+
+
+def test_size_buckets_and_autotuner_default():
+    """Pencils are grouped by the smallest bucket that holds them (the largest bucket takes
+    everything above it); an untuned bucket falls back to the tensor-core engine."""
+    import paper_1504_06443_gb300 as gep
+    assert [gep._bucket(m) for m in (1, 128, 129, 256, 257, 2048, 2049, 4096, 99999)] == \
+        [128, 128, 256, 256, 512, 2048, 4096, 4096, 4096]
+    t = gep.Autotuner()
+    assert t.precision_for(300) == "fp64_emulated"
+    t.choice[512] = "fp64"
+    assert t.precision_for(300) == "fp64" and t.precision_for(600) == "fp64_emulated"
+
+
+def test_make_options_maps_names_to_codes():
+    import paper_1504_06443_gb300 as gep
+    o = gep.make_options(reducer="explicit_inv", sep="2stage", precision="mixed_refined", want_vectors=False,
+                         timers=True, bandwidth=32, refine_iters=3)
+    assert (o.reducer, o.sep, o.precision) == (gep.RED_EXPLICIT_INV, gep.SEP_2STAGE, gep.PREC_MIXED_REFINED)
+    assert (o.want_vectors, o.timers, o.bandwidth, o.refine_iters) == (0, 1, 32, 3)
+    with pytest.raises(KeyError):
+        gep.make_options(sep="3stage")
