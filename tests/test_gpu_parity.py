@@ -2,7 +2,7 @@
 
 Inputs are seeded (gep_inputs); expected values come from the oracle on the same
 inputs.  Sizes span several 64/128-wide tiles plus a ragged tail.  Tolerances are
-the spec FP64 bounds (|d lambda| <= 1e-11 ||A||_2, residual
+the solver's FP64 accuracy target (|d lambda| <= 1e-11 ||A||_2, residual
 ||AY - BY Lambda||_F / (||A||_F M) <= 1e-13, ||Y^T B Y - I||_max <= 1e-12) or, for
 intermediate quantities, a stated multiple of M * eps relative to the input scale.
 """
