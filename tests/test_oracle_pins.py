@@ -178,7 +178,7 @@ def _check_gep(A, B, w, Y, tol_lam=None, lam_ref=None):
 
 @pytest.mark.parametrize("M,seed", [(1, 0), (2, 1), (17, 2), (64, 3), (200, 4)])
 def test_gep_known_spectrum(oracle_lib, M, seed):
-    """Config-1 recipe: exact lambda known; eigenvectors are L0^-T Q up to sign."""
+    """Known-spectrum recipe: exact lambda known; eigenvectors are L0^-T Q up to sign."""
     g = gi.known_spectrum(M, seed)
     w, Y, info = oracle_lib.gep_solve(g["A"], g["B"])
     assert info == 0
