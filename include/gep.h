@@ -22,9 +22,11 @@
  *  - Return value: GEP_OK (0) on success; -i if argument i (1-based) is illegal
  *    (checked on the host before anything is enqueued, LAPACK info < 0
  *    convention); GEP_ERR_* codes below for other failures.
- *  - Numerical status (B not positive definite, D&C not converged) is written to
- *    device memory and read with gep_get_info(); once it is non-zero, later stages
- *    of the same handle become no-ops until gep_reset_info().
+ *  - Numerical status (B not positive definite, D&C not converged) and device-side
+ *    failures (non-finite input, a bounded wait that gave up: GEP_ERR_NONFINITE,
+ *    GEP_ERR_TIMEOUT) are written to device memory and read with gep_get_info();
+ *    once it is non-zero, later stages of the same handle become no-ops until
+ *    gep_reset_info().
  */
 #ifndef GEP_H
 #define GEP_H
