@@ -42,7 +42,10 @@ def parse():
                    help="SEP reduction: 1-stage tridiagonalisation or full->band->tridiagonal")
     p.add_argument("--bandwidth", type=int, default=0, help="band width of --sep 2stage (0: library default 64)")
     p.add_argument("--values-only", action="store_true", help="eigenvalues only (T_evo of the paper's benchmark)")
-    p.add_argument("--cpu-sample-M", type=int, default=2048)
+    p.add_argument("--cpu-sample-M", type=int, nargs="+", default=[1024, 2048, 3072],
+                   help="orders of the oracle solves the c M^3 fit of the CPU baseline is taken over")
+    p.add_argument("--peaks", action="store_true",
+                   help="measure the FP64 peaks of this GPU (cuBLAS DGEMM burst and sustained) and exit")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-check", action="store_true")
@@ -334,7 +337,7 @@ class Clocks:
 
 
 def cpu_sample(M_s, seed):
-    """Oracle (FP64 CPU) full solve of an M_s tight-binding pencil; returns (seconds, cores)."""
+    """Oracle (FP64 CPU) full solve of an M_s tight-binding pencil; returns (seconds, cores, info)."""
     import gep_inputs as gi
     import oracle
     cores = os.cpu_count() or 1
@@ -347,29 +350,170 @@ def cpu_sample(M_s, seed):
     return dt, int(os.environ.get("OMP_NUM_THREADS", cores)), info
 
 
+def cm3_fit(samples, M):
+    """Least-squares fit t = c M^3 over (M_s, seconds) samples, extrapolated to order M."""
+    num = sum(t * float(m) ** 3 for m, t in samples)
+    den = sum(float(m) ** 6 for m, _ in samples)
+    c = num / den
+    return c * float(M) ** 3, c
+
+
+def cpu_baseline_fit(M, sizes, seed):
+    """The oracle as it stands, timed on the host cores at several orders, with the c M^3
+    fit extrapolated to order M (labelled as such)."""
+    samples, cores = [], None
+    for Ms in sizes:
+        dt, cores, _ = cpu_sample(Ms, seed)
+        samples.append((Ms, dt))
+    v, c = cm3_fit(samples, M)
+    return {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "extrapolated": True,
+            "fit": "t = c M^3, least squares", "c_s_per_M3": c,
+            "samples_s": {str(m): round(t, 3) for m, t in samples},
+            "sample": (f"oracle full GEP solves (all eigenpairs) of tight-binding pencils of order "
+                       f"{', '.join(str(m) for m in sizes)} on {cores} host threads; the c M^3 fit is "
+                       f"extrapolated to M={M}")}
+
+
 def run_reference(a, rank, world):
+    """The reference arm: there is no reference implementation of the method (a paper
+    only), so the FP64 CPU oracle is timed as it stands.  Each step is one oracle solve of a
+    bounded sample (orders rotating over --cpu-sample-M); the M = 32768 value is the c M^3 fit
+    of the timed samples, labelled extrapolated."""
     if rank != 0:
         return
-    M, Ms = a.M, a.cpu_sample_M
-    scale = (M / Ms) ** 3
+    M, sizes = a.M, list(a.cpu_sample_M)
     for _ in range(a.warmup):
-        cpu_sample(Ms, a.seed)
-    ts = []
-    cores = None
-    for _ in range(a.steps):
+        cpu_sample(min(sizes), a.seed)
+    samples, cores = [], None
+    t0 = time.perf_counter()
+    for i in range(max(a.steps, len(sizes))):
+        Ms = sizes[i % len(sizes)]
         dt, cores, info = cpu_sample(Ms, a.seed)
-        ts.append(dt)
-    v = sum(ts) / len(ts) * scale
-    sample = (f"oracle full GEP solve (all eigenpairs) of the M={Ms} tight-binding pencil ({Ms // 4} atoms), "
-              f"host time x (M/{Ms})^3 = x{scale:.0f}")
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": a.steps,
+        samples.append((Ms, dt))
+    wall = time.perf_counter() - t0
+    v, c = cm3_fit(samples, M)
+    sample = (f"{len(samples)} oracle full GEP solves (all eigenpairs) of tight-binding pencils of order "
+              f"{', '.join(str(m) for m in sizes)} (rotating) on {cores} host threads; value = the c M^3 "
+              f"least-squares fit extrapolated to M={M}")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": len(samples),
             "warmup": a.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "extrapolated": True,
+            "sample_wall_s": round(wall, 2), "sample_ms_per_step": round(wall / len(samples) * 1e3, 1),
             "config": {"workload": f"tight-binding GEP M={M} ({M // 4} atoms x 4 sp orbitals), all eigenpairs",
-                       "M": M, "seed": a.seed, "sampled_M": Ms},
-            "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+                       "M": M, "seed": a.seed, "sampled_M": sizes},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "extrapolated": True,
+                             "c_s_per_M3": c, "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def fp64_peaks(n=8192, burst_reps=5, sustained_s=3.0):
+    """FP64 throughput of this GPU measured with cuBLAS DGEMM (torch.matmul on float64,
+    2 n^3 flops per call): best of burst_reps calls, and back to back for sustained_s seconds.
+    This is the FP64 tensor-core (DMMA) rate the paper's FP64 solvers would run at."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    c = a @ b
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = None
+    for _ in range(burst_reps):
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None or t < best else best
+    reps = max(1, int(sustained_s / best))
+    e0.record()
+    for _ in range(reps):
+        torch.matmul(a, b, out=c)
+    e1.record()
+    torch.cuda.synchronize()
+    sus = e0.elapsed_time(e1) / 1e3 / reps
+    f = 2.0 * n ** 3
+    del a, b, c
+    torch.cuda.empty_cache()
+    return {"fp64_dgemm_tflops": f / best / 1e12, "fp64_dgemm_tflops_sustained": f / sus / 1e12,
+            "how": f"cuBLAS DGEMM {n}^3 via torch.matmul (float64): best of {burst_reps} (burst) and "
+                   f"{reps} back to back (sustained), CUDA events"}
+
+
+def run_peaks(a):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    out = fp64_peaks()
+    out["gpu"] = torch.cuda.get_device_name()
+    print(json.dumps(out), flush=True)
+
+
+# DRAM traffic of one product-kernel launch from a committed ncu capture
+# (profiles/k_oz_gemm_4096x4096x4096.md: dram__bytes_read.sum + dram__bytes_write.sum of one
+# 4096^3 launch, 36 plane products).  It is scaled to the timed launches by their tensor
+# flops and reported only while the kernel source is the one that was captured.
+OZ_CAPTURE = {"dram_bytes": 4.072e9 + 0.142e9, "tensor_flops": 36 * 2.0 * 4096 ** 3,
+              "kernel_sha1": "b0b9d816fcb173c9c1bacf2c80c1113bd6c532a2",
+              "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 4096^3 k_oz_gemm launch "
+                      "(profiles/k_oz_gemm_4096x4096x4096.md), scaled to the average timed launch by its "
+                      "tensor flops; null when the kernel source differs from the captured one"}
+
+
+def oz_kernel_sha1():
+    """sha1 of the product kernel's source text (from its template line to the end of the
+    kernel), so that a capture taken of another version is not reported."""
+    import hashlib
+    path = os.path.join(ROOT, "paper_1504_06443_gb300", "csrc", "gemm_oz.cu")
+    try:
+        src = open(path).read()
+        i = src.index("template <int SC, int LC>")
+        j = src.index("size_t smem_bytes_for", i)
+        return hashlib.sha1(src[i:j].encode()).hexdigest()
+    except (OSError, ValueError):
+        return None
+
+
+def product_traffic(prof):
+    if not prof["launches"] or OZ_CAPTURE["kernel_sha1"] != oz_kernel_sha1():
+        return None
+    per_launch_flops = prof["tensor_flops"] / prof["launches"]
+    return OZ_CAPTURE["dram_bytes"] * per_launch_flops / OZ_CAPTURE["tensor_flops"]
+
+
+def stage_rooflines(M, stages, band_ms, vectors, sep, b, bf16_peak, f64pk):
+    """Per-stage algorithmic FP64-equivalent flops (the method's counts, not the work the GPU
+    path does) over the stage's CUDA-event time, against the measured FP64 DGEMM rate and, in
+    terms of the 36 BF16 plane products one FP64-accurate product costs, against the measured
+    sustained BF16 rate."""
+    m3 = float(M) ** 3
+    names = ["R1_cholesky", "R2_reduce", "S1_tridiag", "S2_dc", "S3_back_q", "R3_backsub", "MP3_refine"]
+    alg = {"R1_cholesky": m3 / 3, "R2_reduce": m3, "S1_tridiag": 4.0 / 3 * m3,
+           "S2_dc": 4.0 / 3 * m3 if vectors else 0.0,
+           "S3_back_q": (4.0 if sep == "2stage" else 2.0) * m3 if vectors else 0.0,
+           "R3_backsub": m3 if vectors else 0.0, "MP3_refine": 0.0}
+    f64 = f64pk.get("fp64_dgemm_tflops_sustained") if isinstance(f64pk, dict) else None
+    out = {}
+
+    def row(ms, flops, tensor=True):
+        r = {"ms": round(ms, 2), "alg_flops": flops}
+        if ms > 0 and flops > 0:
+            tf = flops / (ms * 1e-3) / 1e12
+            r["fp64_equiv_tflops"] = tf
+            if f64:
+                r["frac_of_fp64_dgemm"] = tf / f64
+            if tensor and bf16_peak:
+                r["frac_of_bf16_sustained_36_planes"] = tf * 36 / bf16_peak
+        return r
+
+    for n, t in zip(names, stages):
+        if alg[n] > 0:
+            out[n] = row(t, alg[n])
+    if band_ms:
+        out["S1b_full_to_band"] = row(band_ms[0], 4.0 / 3 * m3)
+        out["S1c_bulge_chasing"] = row(band_ms[1], 6.0 * b * float(M) ** 2, tensor=False)
+    out["R1+R2_reducer"] = row(stages[0] + stages[1], alg["R1_cholesky"] + alg["R2_reduce"])
+    total = sum(alg.values()) + (6.0 * b * float(M) ** 2 if band_ms else 0.0)
+    return {"stages": out, "whole_solve_alg_flops": total}
 
 
 def sampled_check(A, B, w, Y, ncols=64, seed=0):
@@ -399,6 +543,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.peaks:
+        run_peaks(a)
+        return
     if a.gemm:
         run_gemm(a)
         return
@@ -452,8 +599,13 @@ def main():
         gep.solve_async(A, B, w, Yt, opts, h)
     torch.cuda.synchronize()
     info = h.info()
+    # product-kernel launches per step (one untimed solve with per-launch events), so that the
+    # events of the timed region cover every product launch of every timed step
+    h.profile_enable(1 << 20)
+    gep.solve_async(A, B, w, Yt, opts, h)
+    per_step_products = h.profile_read(reset=True)["launches"]
+    h.profile_enable(per_step_products * a.steps + 64)
     h.launches(reset=True)
-    h.profile_enable(65536)
     clk = Clocks(local)
     clk.start()
     if dist:
@@ -513,28 +665,35 @@ def main():
                "rc": rc, "max_abs_dw_vs_device": float((wh.cuda() - w).abs().max().item())}
 
     pk, pk_kind = peaks()
-    t_kernel_ms = prof["ms"] / a.steps if prof["launches"] else None
+    try:
+        f64pk = fp64_peaks(8192, burst_reps=3, sustained_s=2.0)
+    except Exception as ex:  # the bench line stays valid without it
+        f64pk = {"error": str(ex)}
+    covered_steps = prof["launches"] / per_step_products if per_step_products else 0
+    t_kernel_ms = prof["ms"] / covered_steps if covered_steps else None
     achieved = (prof["tensor_flops"] / (prof["ms"] * 1e-3) / 1e12) if prof["ms"] > 0 else None
     peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
     roof = {"bound": "tensor", "kernel": "k_oz_gemm (split-BF16 tcgen05 product)",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": product_traffic(prof),
+            "traffic_note": OZ_CAPTURE["note"],
             "peak_kind": f"{pk_kind} bf16 dense sustained",
             "fp64_equiv_tflops": (prof["fp64_flops"] / (prof["ms"] * 1e-3) / 1e12) if prof["ms"] > 0 else None,
             "kernel_ms_per_step": t_kernel_ms, "timed_launches": prof["launches"], "untimed_launches": prof["skipped"],
+            "launches_per_step": per_step_products, "steps_covered": covered_steps,
             "share_of_step": (t_kernel_ms / ms) if t_kernel_ms else None}
+
+    bw = (a.bandwidth or 64) if a.sep == "2stage" else 0
+    stage_roof = stage_rooflines(M, stages, band_ms, vectors, a.sep, bw, peak, f64pk)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         del A, B
         torch.cuda.empty_cache()
-        dt, cores, cinfo = cpu_sample(a.cpu_sample_M, a.seed)
-        scale = (M / a.cpu_sample_M) ** 3
-        cpu = {"value": dt * scale, "unit": "s", "cores": cores, "kind": "oracle",
-               "sample": f"oracle full GEP solve of the M={a.cpu_sample_M} tight-binding pencil "
-                         f"({a.cpu_sample_M // 4} atoms) took {dt:.2f} s; scaled by (M/{a.cpu_sample_M})^3"}
+        cpu = cpu_baseline_fit(M, list(a.cpu_sample_M), a.seed)
 
-    flops_alg = ((1.0 / 3 + 2.0 + 4.0 / 3 + 8.0 / 3 + 2.0 + 1.0) if vectors else (1.0 / 3 + 2.0 + 4.0 / 3)) * float(M) ** 3
+    flops_alg = stage_roof["whole_solve_alg_flops"]
     if rank == 0:
         line = {"metric": METRIC, "value": ms_max / 1e3, "unit": "s", "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
@@ -554,7 +713,8 @@ def main():
                 if band_ms else None,
                 "info": info, "gpu_launches": int(launches),
                 "fp64_equiv_tflops_whole_solve": flops_alg / (ms_max * 1e-3) / 1e12,
-                "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "check": check}
+                "roofline": roof, "stage_roofline": stage_roof["stages"], "fp64_peak": f64pk,
+                "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "check": check}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

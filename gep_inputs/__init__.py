@@ -59,10 +59,12 @@ def known_spectrum(M: int, seed: int):
     return dict(A=np.ascontiguousarray(A), B=np.ascontiguousarray(B), lam=lam, L0=L0, Q=Q)
 
 
-def clustered_spectrum(M: int, seed: int):
+def clustered_spectrum(M: int, seed: int, big: int = 0):
     """known_spectrum's construction with tight clusters planted in the spectrum: groups
     of 2..6 eigenvalues spaced 1e-9 apart and groups of exactly repeated eigenvalues
-    (the case first-order eigenpair corrections cannot take).  Returns dict(A, B, lam)."""
+    (the case first-order eigenpair corrections cannot take).  big > 0 also plants one
+    run of `big` consecutive eigenvalues spaced 1e-9 apart in the middle of the spectrum.
+    Returns dict(A, B, lam)."""
     rng = np.random.default_rng(seed)
     L0 = np.tril(rng.normal(0.0, 0.05, size=(M, M)), -1)
     L0[np.diag_indices(M)] = rng.uniform(1.0, 2.0, size=M)
@@ -78,6 +80,9 @@ def clustered_spectrum(M: int, seed: int):
         else:
             lam[i:i + k] = lam[i]
         i += k + int(rng.integers(5, 40))
+    if big > 0:
+        s0 = (M - big) // 2
+        lam[s0:s0 + big] = 1.5 + 1e-9 * np.arange(big)
     X = L0 @ Q
     A = (X * lam[None, :]) @ X.T
     A = 0.5 * (A + A.T)

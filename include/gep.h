@@ -176,7 +176,9 @@ int gep_solve_host(gep_handle_t h, int M, const double* A, int lda, const double
  * First-order perturbation of Eq. 2: Abar = Y G Y^T, Bbar = Y H Y^T with G, H built from
  * lbar, lambda and What = Y^T W Y on the occupied/virtual blocks (only occupied/virtual
  * gaps are divided by).  lbar: M weights (NULL = 1 for occupied, 0 for virtual); W:
- * symmetric M x M (lower read; NULL = no density term).  All pointers are device memory;
+ * M x M, both triangles read (NULL = no density term); since P is symmetric only the
+ * symmetric part (W + W^T) / 2 enters the loss, and that is what the library forms, so a
+ * raw gradient with respect to P can be passed as it is.  All pointers are device memory;
  * the workspace must hold gep_adjoint_workspace_size bytes.  Dense products run on the
  * FP64-accurate tensor-core engine. */
 int gep_adjoint_workspace_size(gep_handle_t h, int M, int n_occ, size_t* bytes);
@@ -217,6 +219,15 @@ int gep_reset_info(gep_handle_t h);
  * Returns -2 / -3 for an out-of-range drop_sweep / wait_limit_s.  Clear the recorded error
  * with gep_reset_info. */
 int gep_set_wait_fault(gep_handle_t h, int drop_sweep, double wait_limit_s);
+
+/* Test hook for the panel QR of the full -> band reduction (S1b).  By default each panel
+ * is factorised in one cooperative launch whose CTAs keep 64, 128 or 256 panel rows each
+ * in shared memory (the fewest rows whose grid is resident at once), and by one launch
+ * per column step when no such grid exists.  rows = 64, 128 or 256 forces that CTA height
+ * (a panel whose grid would not be resident then returns GEP_ERR_UNSUPPORTED), rows = -1
+ * forces the per-column-step kernel, rows = 0 restores the automatic choice.  Returns -2
+ * for any other value. */
+int gep_set_panel_qr(gep_handle_t h, int rows);
 
 /* Per-stage times (ms) of the last gep_solve with o->timers = 1:
  * t[0] Cholesky (R1), t[1] reduction (R2), t[2] tridiagonalisation (TRD/BAND),
@@ -286,6 +297,9 @@ int gep_dgemm(gep_handle_t h, char transa, char transb, char uplo, int m, int n,
  *  - All calls share the one array and it keeps the last call's contents; calls that
  *    overlap on the GPU (other streams, other threads) race on it.  Serialise them.
  *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ *  - A failure on the GPU after the call has returned (a bounded wait inside the product
+ *    kernel that gave up) cannot be a return code: the last kernel of the call then fills
+ *    every element of C the call writes with NaN, so such a failure shows in C.
  * Returns 0, -i for an illegal argument i, GEP_ERR_TOO_LARGE or GEP_ERR_CUDA. */
 int gep_dgemm_emulated_noalloc(char transa, char transb, char uplo, int m, int n, int k, double alpha,
                                const double* A, int lda, const double* B, int ldb, double beta, double* C,

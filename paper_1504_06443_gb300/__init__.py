@@ -94,6 +94,7 @@ def load():
             "gep_get_info": (_I, [_P, ctypes.POINTER(_I)]),
             "gep_reset_info": (_I, [_P]),
             "gep_set_wait_fault": (_I, [_P, _I, _D]),
+            "gep_set_panel_qr": (_I, [_P, _I]),
             "gep_get_stage_times": (_I, [_P, ctypes.POINTER(_D)]),
             "gep_launch_count": (ctypes.c_longlong, [_P, _I]),
             "gep_refine_steps": (_I, [_P]),
@@ -256,6 +257,11 @@ class Handle:
         (at most 4) with GEP_ERR_TIMEOUT; drop_sweep >= 0 stops that bulge-chasing sweep from
         publishing progress, so the wait behind it runs out (-1: no injection)."""
         _check(self.lib.gep_set_wait_fault(self.h, int(drop_sweep), float(wait_limit_s)), "gep_set_wait_fault")
+
+    def set_panel_qr(self, rows=0):
+        """Test hook: force the panel-QR CTA height of the full -> band reduction (64, 128 or
+        256 rows per CTA), the per-column-step kernel (-1), or the automatic choice (0)."""
+        _check(self.lib.gep_set_panel_qr(self.h, int(rows)), "gep_set_panel_qr")
 
     def stage_times(self):
         t = (_D * 7)()
@@ -586,7 +592,8 @@ def adjoint(w, Y, n_occ, lbar=None, W=None, handle=None):
     """(Abar, Bbar) of loss = sum_k lbar_k lambda_k + <W, Y_o Y_o^T> (gep_adjoint).
 
     w: eigenvalues ascending, Y: B-orthonormal eigenvectors (both from solve);
-    lbar: M weights (None = 1 on the n_occ occupied, 0 elsewhere); W: symmetric or None."""
+    lbar: M weights (None = 1 on the n_occ occupied, 0 elsewhere); W: M x M or None (both
+    triangles are read; the library uses its symmetric part (W + W^T) / 2)."""
     torch = _torch()
     _need_vector(w, "w", 0, cuda=False)
     M = int(w.shape[0])
@@ -639,8 +646,8 @@ def _autograd_function():
             lbar = None if gw is None else gw.contiguous()
             if lbar is None:
                 lbar = torch.zeros_like(w)
-            W = None if gP is None else 0.5 * (gP + gP.t())
-            Ab, Bb = adjoint(w, Yc, ctx.n_occ, lbar, W)
+            # gep_adjoint reads both triangles of the cotangent and uses its symmetric part
+            Ab, Bb = adjoint(w, Yc, ctx.n_occ, lbar, gP)
             return Ab.contiguous(), Bb.contiguous(), None, None
 
     return GEPDensity

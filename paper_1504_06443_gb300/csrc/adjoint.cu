@@ -52,14 +52,14 @@ size_t adjoint_ws_elems(int M, int no) {
 int adjoint(gep_handle_t h, int M, int no, const double* w, const double* Y, int ldy, const double* lbar,
             const double* W, int ldw, double* Abar, double* Bbar, int ldab, double* ws, int engine) {
   auto r = [](size_t n) { return (n + 31) & ~(size_t)31; };
-  double* X1 = ws;                         // W (full) then G
+  double* X1 = ws;                         // (W + W^T) / 2, then G
   double* X2 = X1 + r((size_t)M * M);      // W Y then H
   double* X3 = X2 + r((size_t)M * M);      // G Y^T / H Y^T
   double* Wh = X3 + r((size_t)M * M);      // Y_o^T W Y  (no x M)
   const double* Whp = nullptr;
   if (W && no > 0) {
-    GEP_CHECK(copy_lower(h, M, W, ldw, X1, M));
-    GEP_CHECK(symmetrize_lower(h, M, X1, M));
+    // <W, P> with P symmetric only sees the symmetric part of W: both triangles are read
+    GEP_CHECK(symmetric_part(h, M, W, ldw, X1, M));
     GEP_CHECK(dgemm(h, 'N', 'N', 'F', M, M, M, 1.0, X1, M, Y, ldy, 0.0, X2, M, engine));     // W Y
     GEP_CHECK(dgemm(h, 'T', 'N', 'F', no, M, M, 1.0, Y, ldy, X2, M, 0.0, Wh, no, engine));   // Y_o^T W Y
     Whp = Wh;

@@ -219,6 +219,13 @@ int gep_set_wait_fault(gep_handle_t h, int drop_sweep, double wait_limit_s) {
   return GEP_OK;
 }
 
+int gep_set_panel_qr(gep_handle_t h, int rows) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (rows != 0 && rows != -1 && rows != 64 && rows != 128 && rows != 256) return -2;
+  h->pqr_rows = rows;
+  return GEP_OK;
+}
+
 long long gep_launch_count(gep_handle_t h, int reset) {
   if (!handle_ok(h)) return -1;
   long long n = h->launches;

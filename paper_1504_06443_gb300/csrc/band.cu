@@ -750,18 +750,30 @@ int panel_factor(gep_handle_t h, int n, int b, double* P, int ldp, double* tau, 
   const int nref = n < b ? n : b;
   double *pin = w.part0, *pout = w.part1, *rin = w.prow0, *rout = w.prow1;
   // one cooperative launch when every CTA of the panel can be resident at once
-  static int coop_per_sm = -1;
-  if (coop_per_sm < 0) {
+  static int per_sm_of[64];
+  static unsigned long long devices = 0;
+  int dev = 0;
+  GEP_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return GEP_ERR_UNSUPPORTED;
+  if (first_use_on_device(devices)) {
     const size_t smax = pqr_coop_smem_bytes(PQ_ROWS, BMAX);
     GEP_CUDA(cudaFuncSetAttribute(k_pqr_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
-    GEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&coop_per_sm, k_pqr_coop, PQ_ROWS, smax));
+    GEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_of[dev], k_pqr_coop, PQ_ROWS, smax));
   }
+  const int coop_per_sm = per_sm_of[dev];
   // fewest rows per CTA whose grid is resident at once and fits the partial-sum buffers
+  // (a test may force 64, 128 or 256 rows, or the per-column kernel with -1)
   const long long cap = (long long)coop_per_sm * h->sm_count;
   int rp = 0;
-  for (int c = 64; c <= PQ_ROWS; c *= 2) {
-    long long g = (n + c - 1) / c;
-    if (g <= cap && g <= w.gcap) { rp = c; break; }
+  if (h->pqr_rows > 0) {
+    const long long g = (n + h->pqr_rows - 1) / h->pqr_rows;
+    if (g > cap || g > w.gcap) return GEP_ERR_UNSUPPORTED;
+    rp = h->pqr_rows;
+  } else if (h->pqr_rows == 0) {
+    for (int c = 64; c <= PQ_ROWS; c *= 2) {
+      long long g = (n + c - 1) / c;
+      if (g <= cap && g <= w.gcap) { rp = c; break; }
+    }
   }
   if (rp > 0) {
     const int Gc = (n + rp - 1) / rp;
@@ -895,11 +907,9 @@ int band_to_tridiag(gep_handle_t h, int M, const double* C, int ldc, int b, doub
     const int Q = (M - 2) / b;
     if (q2) GEP_CUDA(cudaMemsetAsync(q2, 0, q2_elems(M, b) * sizeof(double), h->stream));
     size_t smem = bulge_smem_bytes();
-    static int attr_done = 0;
-    if (!attr_done) {
+    static unsigned long long attr_devices = 0;
+    if (first_use_on_device(attr_devices))
       GEP_CUDA(cudaFuncSetAttribute(k_bulge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      attr_done = 1;
-    }
     int per_sm = 0;
     GEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bulge, 256, smem));
     if (per_sm < 1) return GEP_ERR_UNSUPPORTED;
@@ -942,12 +952,10 @@ int apply_q2(gep_handle_t h, int M, int b, const double* q2, double* Z, int ldz,
     double* U = ws;
     double* Tmp = ws + rr((size_t)(Q / TQ + 1) * W * W);
     size_t smem = q2_tile_smem_bytes(b);
-    static int attr_done = 0;
-    if (!attr_done) {
+    static unsigned long long attr_devices = 0;
+    if (first_use_on_device(attr_devices))
       GEP_CUDA(cudaFuncSetAttribute(k_q2_tile_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)q2_tile_smem_bytes(BMAX)));
-      attr_done = 1;
-    }
     for (int J = nJ - 1; J >= 0; --J) {
       const int nK = (Q - J * TQ) / TQ + 1;  // tiles (J, K) with a diamond: K TQ <= Q - J TQ
       k_q2_tile_build<<<dim3(nK, (W + TB_COLS - 1) / TB_COLS), 256, smem, h->stream>>>(M, b, Q, J, q2, U,
@@ -972,12 +980,10 @@ int apply_q2(gep_handle_t h, int M, int b, const double* q2, double* Z, int ldz,
     return GEP_OK;
   }
   size_t smem = q2_smem_bytes(b);
-  static int attr_done = 0;
-  if (!attr_done) {
+  static unsigned long long attr_devices = 0;
+  if (first_use_on_device(attr_devices))
     GEP_CUDA(cudaFuncSetAttribute(k_q2_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)q2_smem_bytes(BMAX)));
-    attr_done = 1;
-  }
   const int slabs = (ncol + Q2_COLS - 1) / Q2_COLS;
   for (int wt = 0; wt <= 2 * Q; ++wt) {
     int kmin = wt - Q > 0 ? wt - Q : 0, kmax = wt / 2;

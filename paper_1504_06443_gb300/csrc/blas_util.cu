@@ -60,6 +60,22 @@ __global__ void k_symmetrize(int M, double* A, int lda) {
   }
 }
 
+// X = (W + W^T) / 2: tile (bi, bj) of W and the transposed tile (bj, bi), both read
+// through shared memory so every access is coalesced.
+__global__ void k_sym_part(int M, const double* __restrict__ W, int ldw, double* __restrict__ X, int ldx) {
+  __shared__ double t[32][33];
+  int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {  // t[c][r'] = W(j0 + r, i0 + c)
+    int i = j0 + threadIdx.x, j = i0 + r;
+    if (i < M && j < M) t[threadIdx.x][r] = W[GEP_IX(i, j, ldw)];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int i = i0 + threadIdx.x, j = j0 + r;  // X(i, j) = (W(i, j) + W(j, i)) / 2
+    if (i < M && j < M) X[GEP_IX(i, j, ldx)] = 0.5 * (W[GEP_IX(i, j, ldw)] + t[r][threadIdx.x]);
+  }
+}
+
 __global__ void k_zero_upper(int M, double* A, int lda) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   for (int j = blockIdx.y; j < M; j += gridDim.y)
@@ -129,6 +145,13 @@ int symmetrize_lower(gep_handle_t h, int M, double* A, int lda) {
   if (M <= 1) return GEP_OK;
   dim3 g((M + 31) / 32, (M + 31) / 32);
   k_symmetrize<<<g, dim3(32, 8), 0, h->stream>>>(M, A, lda);
+  return check_launch(h);
+}
+
+int symmetric_part(gep_handle_t h, int M, const double* W, int ldw, double* X, int ldx) {
+  if (M <= 0) return GEP_OK;
+  dim3 g((M + 31) / 32, (M + 31) / 32);
+  k_sym_part<<<g, dim3(32, 8), 0, h->stream>>>(M, W, ldw, X, ldx);
   return check_launch(h);
 }
 

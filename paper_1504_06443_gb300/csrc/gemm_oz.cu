@@ -651,12 +651,11 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
   long long kp_fit = (long long)((cap - fixed) / per_k) / TK * TK;
   int KP = (int)(kp_fit < KP_MAX ? kp_fit : KP_MAX);
   if (KP < TK) return GEP_ERR_ALLOC;
-  static int attr_done = 0;
-  if (!attr_done) {
+  static unsigned long long attr_devices = 0;
+  if (first_use_on_device(attr_devices)) {
     cudaFuncSetAttribute(k_oz_gemm<8, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes_for(MAXS));
     cudaFuncSetAttribute(k_oz_gemm<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes_for(MAXS));
     cudaFuncSetAttribute(k_oz_gemm<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes_for(MAXS));
-    attr_done = 1;
   }
   int lower = (uplo == 'L' || uplo == 'l');
   for (int kb = 0; kb < k; kb += KP) {
@@ -750,6 +749,22 @@ constexpr size_t kNoallocBytes = 64u << 20;
 constexpr int kNoallocMaxDevices = 64;
 void* g_noalloc_ptr[kNoallocMaxDevices] = {};
 int g_noalloc_ready[kNoallocMaxDevices] = {};
+
+// The call returns before the GPU runs the product, so a device-side failure (a bounded
+// wait of the product kernel that gave up and set the status word) cannot be a return
+// code.  This kernel runs last in the call and, only when the status word is set, fills
+// every element of C that the call writes with NaN: the failure then shows in C itself.
+__global__ void k_noalloc_poison(int m, int n, double* __restrict__ C, int ldc, int lower, const int* st) {
+  if (st[0] == 0 && st[1] == 0) return;
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  const long long total = (long long)m * n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % m), j = (int)(idx / m);
+    if (lower && i < j) continue;
+    C[(size_t)i + (size_t)j * ldc] = nan;
+  }
+}
 }  // namespace
 
 extern "C" int gep_dgemm_emulated_noalloc(char transa, char transb, char uplo, int m, int n, int k, double alpha,
@@ -795,5 +810,10 @@ extern "C" int gep_dgemm_emulated_noalloc(char transa, char transb, char uplo, i
   if (cudaMemsetAsync(h.d_status, 0, status_bytes, h.stream) != cudaSuccess) return GEP_ERR_CUDA;
   int rc = gep::dgemm_oz(&h, transa, transb, uplo, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 9);
   h.magic = 0;
-  return rc;
+  if (rc != GEP_OK) return rc;
+  const long long total = (long long)m * n;
+  const int blocks = (int)((total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024);
+  k_noalloc_poison<<<blocks, 256, 0, h.stream>>>(m, n, C, ldc, (uplo == 'L' || uplo == 'l') ? 1 : 0, h.d_status);
+  if (cudaGetLastError() != cudaSuccess) return GEP_ERR_CUDA;
+  return GEP_OK;
 }

@@ -23,6 +23,9 @@ struct gep_handle_s {
   // releases of one bulge-chasing sweep so that the waits behind it run out
   unsigned long long wait_limit_ns = 4000000000ull;
   int fault_drop_sweep = -1;
+  // test hook: rows per CTA of the single-launch panel QR (64, 128 or 256), -1 for the
+  // one-launch-per-column kernel, 0 for the automatic choice
+  int pqr_rows = 0;
   int magic = 0x6e70;
   cudaEvent_t ev[8] = {};
   cudaEvent_t ev_band = nullptr;  // between full->band and bulge chasing (two-stage, timers on)
@@ -67,6 +70,18 @@ struct Arena {
 
 // Counting-only arena: used by workspace queries to size the same carving.
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Kernel attributes (the dynamic shared-memory limit) belong to a device context, so
+// one-time settings are made once per device: `mask` (one per call site) records the
+// devices already done.  Returns true on the first call for the current device.
+inline bool first_use_on_device(unsigned long long& mask) {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return true;
+  const unsigned long long bit = 1ull << d;
+  if (mask & bit) return false;
+  mask |= bit;
+  return true;
+}
 
 inline int check_launch(gep_handle_t h) {
   h->launches++;
@@ -113,6 +128,7 @@ int set_matrix(gep_handle_t h, int m, int n, double offdiag, double diag, double
 int symmetrize_lower(gep_handle_t h, int M, double* A, int lda);  // upper := lower^T
 int transpose(gep_handle_t h, int m, int n, const double* src, int lds, double* dst, int ldd);
 int zero_upper(gep_handle_t h, int M, double* A, int lda);          // strict upper := 0
+int symmetric_part(gep_handle_t h, int M, const double* W, int ldw, double* X, int ldx);  // X = (W + W^T) / 2
 int scan_nonfinite(gep_handle_t h, int M, const double* A, int lda);  // lower triangle
 
 // ---- triangular building blocks (tri.cu) ----

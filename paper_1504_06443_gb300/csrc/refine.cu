@@ -92,7 +92,9 @@ __global__ void k_pair_far(int M, const double* __restrict__ S, const double* __
 
 // Clusters = unions of the overlapping index ranges [i, far[i]] (serial scan, one
 // thread): cstart/csize/coff (scratch offset) per cluster, ncl[0] = number of clusters,
-// cid[i] = the cluster of index i when that cluster is solved exactly (k <= KMAX), else -1.
+// cid[i] = the cluster of index i when that cluster is solved exactly (k <= KMAX),
+// -2 - c when i lies in cluster c of more than KMAX members (chained near-degenerate
+// eigenvalues; its inner pairs only get their B-orthogonality restored), else -1.
 // Scratch use is sum 3 k^2 <= 3 M min(M, KMAX).
 __global__ void k_clusters(int M, const int* __restrict__ far, int* cstart, int* csize, long long* coff, int* cid,
                            int* ncl, const int* st) {
@@ -112,7 +114,7 @@ __global__ void k_clusters(int M, const int* __restrict__ far, int* cstart, int*
       coff[nc] = used;
       if (k <= KMAX) used += 3LL * k * k;
     }
-    for (int q = i; q <= end; ++q) cid[q] = (k > 1 && k <= KMAX) ? nc : -1;
+    for (int q = i; q <= end; ++q) cid[q] = (k > 1 && k <= KMAX) ? nc : (k > KMAX ? -2 - nc : -1);
     if (k > 1) ++nc;
     i = end + 1;
   }
@@ -142,6 +144,11 @@ __global__ void k_refine_E(int M, const double* __restrict__ S, const double* __
       m = fmax(m, fabs(2.0 * e));
     } else if (cid[i] >= 0 && cid[i] == cid[j]) {
       e = 0.0;
+      m = fmax(m, fabs(rij));
+    } else if (cid[i] <= -2 && cid[i] == cid[j]) {
+      // inside a cluster too large to solve exactly the first-order step may be large
+      // (gap below the error level): restore B-orthogonality only
+      e = -0.5 * rij;
       m = fmax(m, fabs(rij));
     } else {
       double gap = lam[j] - lam[i];

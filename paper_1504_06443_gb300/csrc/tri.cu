@@ -110,11 +110,10 @@ __global__ void __launch_bounds__(256) k_inv_diag(int M, const double* L, int ld
 constexpr size_t kSmemDiag = (size_t)NB * NB * sizeof(double) + NB * sizeof(double);
 
 int set_smem_attr() {
-  static int done = 0;
-  if (!done) {
+  static unsigned long long devices = 0;
+  if (first_use_on_device(devices)) {
     cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDiag);
     cudaFuncSetAttribute(k_inv_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDiag);
-    done = 1;
   }
   return GEP_OK;
 }

@@ -70,6 +70,9 @@ def test_host_checks_without_gpu(libpath):
     lib.gep_set_wait_fault.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
     lib.gep_set_wait_fault.restype = ctypes.c_int
     assert lib.gep_set_wait_fault(None, 0, 0.05) == -104
+    lib.gep_set_panel_qr.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.gep_set_panel_qr.restype = ctypes.c_int
+    assert lib.gep_set_panel_qr(None, 64) == -104
     lib.gep_reset_info.argtypes = [ctypes.c_void_p]
     lib.gep_reset_info.restype = ctypes.c_int
     assert lib.gep_reset_info(None) == -104

@@ -25,7 +25,10 @@ def _check_line(line, n_gpus):
     assert line["value"] > 0 and abs(line["ms_per_step"] - 1e3 * line["value"]) <= 1e-9 * line["ms_per_step"]
     assert "workload" in line["config"] and line["config"]["M"] == 32768
     cb = line["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and "M=128" in cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and "128" in cb["sample"]
+    # the M = 32768 figure is a c M^3 fit of the timed samples, and says so
+    assert line["extrapolated"] is True and cb["extrapolated"] is True and line["config"]["sampled_M"] == [128]
+    assert abs(cb["c_s_per_M3"] * 32768.0 ** 3 - line["value"]) <= 1e-9 * line["value"]
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
 

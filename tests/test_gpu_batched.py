@@ -67,3 +67,66 @@ def test_autotuner_picks_an_engine_per_bucket(gep):
     choice = tuner.tune(As, Bs, reps=1)
     assert set(choice) == {128, 512}
     assert all(v in ("fp64", "fp64_emulated") for v in choice.values())
+
+
+def _two_norm(A):
+    return float(np.max(np.abs(np.linalg.eigvalsh(A))))
+
+
+@pytest.fixture(scope="module")
+def batch_vs_oracle(oracle_lib):
+    """24 tight-binding pencils shaped like the batched workload (orders log-uniform in
+    [64, 2048], multiples of 4, the largest order 2048 included), each with the oracle's
+    full FP64 solve and its 2-norm."""
+    orders = gi.batch_orders(24, seed=1234)
+    orders[int(np.argmax(orders))] = 2048
+    pencils = []
+    for i, M in enumerate(orders):
+        tb = gi.tight_binding(M, seed=5000 + i)
+        w_ref, Y_ref, info = oracle_lib.gep_solve(tb["A"], tb["B"])
+        assert info == 0
+        pencils.append(dict(A=tb["A"], B=tb["B"], w=w_ref, Y=Y_ref, nA=_two_norm(tb["A"])))
+    return orders, pencils
+
+
+def _check_against_oracle(results, pencils, what):
+    for i, ((w, Y), p) in enumerate(zip(results, pencils)):
+        A, B, nA = p["A"], p["B"], p["nA"]
+        M = A.shape[0]
+        wh, Yh = w.cpu().numpy(), Y.cpu().numpy()
+        dl = float(np.max(np.abs(wh - p["w"])))
+        assert dl <= 1e-11 * nA, (what, i, M, dl)
+        res = np.linalg.norm(A @ Yh - (B @ Yh) * wh[None, :]) / (np.linalg.norm(A) * M)
+        assert res <= 1e-13, (what, i, M, res)
+        orth = float(np.max(np.abs(Yh.T @ B @ Yh - np.eye(M))))
+        assert orth <= 1e-12, (what, i, M, orth)
+        # isolated eigenpairs compare element by element (both sides apply the sign convention)
+        gaps = np.minimum(np.diff(p["w"], prepend=-np.inf), np.diff(p["w"], append=np.inf))
+        iso = gaps > 1e-6 * nA
+        if iso.any():
+            assert float(np.max(np.abs(Yh[:, iso] - p["Y"][:, iso]))) <= 1e-8, (what, i, M)
+
+
+@pytest.mark.parametrize("precision", ["fp64_emulated", "mixed_refined"])
+def test_batched_workload_shapes_vs_oracle(gep, batch_vs_oracle, precision):
+    """Every pencil of a batch spanning the batched workload's order range, solved on
+    concurrent streams (eager, then replayed from one captured CUDA graph into zeroed output
+    buffers), matches the FP64 oracle at the FP64 tolerances: eigenvalues, residual,
+    B-orthonormality, and isolated eigenvectors element by element."""
+    import torch
+    orders, pencils = batch_vs_oracle
+    As = [dev(p["A"]) for p in pencils]
+    Bs = [dev(p["B"]) for p in pencils]
+    bs = gep.BatchedSolver(As, Bs, nstreams=8, precision=precision)
+    bs.run()
+    torch.cuda.synchronize()
+    assert bs.info() == 0
+    _check_against_oracle(bs.results(), pencils, "eager")
+    bs.capture()
+    for w, Yt in zip(bs.w, bs.Yt):
+        w.zero_()
+        Yt.zero_()
+    bs.replay()
+    torch.cuda.synchronize()
+    assert bs.info() == 0
+    _check_against_oracle(bs.results(), pencils, "graph")

@@ -75,3 +75,22 @@ def test_mixed_fixed_step_count(gep):
     assert h.refine_steps() == 3
     gep.solve(dev(tb["A"]), dev(tb["B"]), precision="mixed_refined", handle=h)
     assert 1 <= h.refine_steps() <= 8
+
+
+def test_mixed_oversize_cluster(gep):
+    """A run of 40 eigenvalues spaced 1e-9 apart chains into one cluster larger than the 32
+    the refinement solves exactly; its inner pairs then only get their B-orthogonality
+    restored.  The refined eigenpairs must still reach the FP64 tolerances."""
+    M = 384
+    g = gi.clustered_spectrum(M, seed=12, big=40)
+    A, B = g["A"], g["B"]
+    h = gep.Handle()
+    w, Y, info = gep.solve(dev(A), dev(B), precision="mixed_refined", handle=h)
+    assert info == 0
+    assert 1 <= h.refine_steps() <= 8
+    wh, Yh = w.cpu().numpy(), Y.cpu().numpy()
+    assert np.max(np.abs(wh - np.sort(g["lam"]))) <= 1e-11 * 20.0
+    res = np.linalg.norm(A @ Yh - (B @ Yh) * wh[None, :]) / (np.linalg.norm(A) * M)
+    orth = np.max(np.abs(Yh.T @ B @ Yh - np.eye(M)))
+    assert res <= 1e-13, res
+    assert orth <= 1e-12, orth

@@ -166,3 +166,65 @@ def test_solve_2stage_q2_tiles(gep, oracle_lib, M, b, precision):
     orth = np.max(np.abs(Yh.T @ B @ Yh - np.eye(M)))
     assert res <= 1e-13, res
     assert orth <= 1e-12, orth
+
+
+_ORACLE_2STAGE = {}
+
+
+@pytest.mark.parametrize("rows", [64, 128, 256, -1])
+@pytest.mark.parametrize("M", [640, 2100])
+def test_solve_2stage_each_panel_qr_form(gep, oracle_lib, rows, M):
+    """The panel QR of the full -> band reduction runs in one launch whose CTAs hold 64, 128
+    or 256 panel rows (the fewest rows whose grid is resident), or one launch per column
+    step where no such grid exists.  Below M ~ 2100 the automatic choice is always 64 rows,
+    so every form is forced through the test hook and the whole benchmark route (two-stage,
+    FP64-accurate tensor-core products) is checked against the oracle: eigenvalues,
+    residual, B-orthonormality and isolated eigenvectors element by element."""
+    tb = gi.tight_binding(M, seed=M + 3)
+    A, B = tb["A"], tb["B"]
+    if M not in _ORACLE_2STAGE:
+        w_ref, Y_ref, info = oracle_lib.gep_solve(A, B)
+        assert info == 0
+        _ORACLE_2STAGE[M] = (w_ref, Y_ref, float(np.max(np.abs(np.linalg.eigvalsh(A)))))
+    w_ref, Y_ref, nA = _ORACLE_2STAGE[M]
+    h = gep.Handle()
+    h.set_panel_qr(rows)
+    try:
+        w, Y, info = gep.solve(dev(A), dev(B), sep="2stage", precision="fp64_emulated", handle=h)
+    finally:
+        h.set_panel_qr(0)
+    assert info == 0
+    wh, Yh = host(w), host(Y)
+    assert np.max(np.abs(wh - w_ref)) <= 1e-11 * nA
+    res = np.linalg.norm(A @ Yh - (B @ Yh) * wh[None, :]) / (np.linalg.norm(A) * M)
+    orth = np.max(np.abs(Yh.T @ B @ Yh - np.eye(M)))
+    assert res <= 1e-13, res
+    assert orth <= 1e-12, orth
+    gaps = np.minimum(np.diff(w_ref, prepend=-np.inf), np.diff(w_ref, append=np.inf))
+    iso = gaps > 1e-6 * nA
+    assert np.max(np.abs(Yh[:, iso] - Y_ref[:, iso])) <= 1e-8
+
+
+@pytest.mark.parametrize("rows", [64, 256, -1])
+def test_tridiag_2stage_spectrum_each_panel_qr_form(gep, oracle_lib, rows):
+    """Stage level: the tridiagonal matrix produced with each panel-QR form has the
+    oracle's spectrum of C (Sturm bisection on the GPU's d, e)."""
+    M, b = 1500, 64
+    C = gi.random_symmetric(M, seed=91)
+    w_ref = oracle_eigs(oracle_lib, C)
+    h = gep.Handle()
+    h.set_panel_qr(rows)
+    try:
+        d, e, tau1, q2, Cb = gep.tridiag_2stage(dev(C), b=b, want_q2=False, handle=h)
+    finally:
+        h.set_panel_qr(0)
+    wT = np.sort(oracle_lib.bisect(host(d), host(e)))
+    nC = max(np.max(np.abs(w_ref)), 1.0)
+    assert np.max(np.abs(wT - w_ref)) <= 200 * M * EPS * nC
+
+
+def test_panel_qr_hook_rejects_bad_values(gep):
+    h = gep.Handle()
+    for bad in (1, 32, 512, -2):
+        with pytest.raises(gep.GepError):
+            h.set_panel_qr(bad)

@@ -3,9 +3,11 @@
 gep_dgemm_emulated_noalloc serves callers that cannot call cudaMalloc (a framework
 that owns all device memory through its own pool, a latency-critical loop that must
 not let a library allocate mid-run): its scratch is a fixed device array inside the
-library.  Its result must match the handle-based gep_dgemm with the same engine to
-the rounding bound the engine tests use, on two calls in a row (the second call runs
-on the scratch the first one left behind).  This file is collected last on purpose.
+library.  Its result must match the handle-based gep_dgemm with the same engine, and the
+plain FP64 product alpha op(A) op(B) + beta C computed on the host, to the rounding bound
+the engine tests use, on two calls in a row (the second call runs on the scratch the first
+one left behind).  This file sorts after every other test file on purpose, so that a run
+stopping at its first failure has already run the rest.
 """
 import ctypes
 
@@ -46,7 +48,8 @@ def _noalloc(f, ta, tb, A, B, C, alpha, beta):
     return rc
 
 
-@pytest.mark.parametrize("ta,tb,m,n,k", [(b"N", b"N", 300, 200, 500), (b"T", b"N", 257, 130, 5000)])
+@pytest.mark.parametrize("ta,tb,m,n,k", [(b"N", b"N", 300, 200, 500), (b"T", b"N", 257, 130, 5000),
+                                         (b"N", b"T", 129, 65, 33)])
 def test_noalloc_matches_handle_path_twice(lib, ta, tb, m, n, k):
     import torch
     g, f = lib
@@ -64,7 +67,12 @@ def test_noalloc_matches_handle_path_twice(lib, ta, tb, m, n, k):
         Ao = Ah.T if ta == b"T" else Ah
         Bo = Bh.T if tb == b"T" else Bh
         bound = 1e-14 * (1.25 * np.abs(Ao) @ np.abs(Bo) + 0.5 * np.abs(Ch))
-        diff = np.abs(out.cpu().numpy() - ref.cpu().numpy())
+        got = out.cpu().numpy()
+        assert np.all(np.isfinite(got)), call  # NaN would mean a device-side failure
+        diff = np.abs(got - ref.cpu().numpy())
+        assert np.all(diff <= bound), (call, float(diff.max()))
+        exact = 1.25 * (Ao @ Bo) - 0.5 * Ch  # plain FP64 product on the host
+        diff = np.abs(got - exact)
         assert np.all(diff <= bound), (call, float(diff.max()))
 
 
