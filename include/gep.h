@@ -49,9 +49,11 @@ typedef struct gep_handle_s* gep_handle_t;
 #define GEP_ERR_UNSUPPORTED (-105) /* option combination not implemented            */
 #define GEP_ERR_TOO_LARGE (-106)   /* exceeds the fixed scratch of gep_dgemm_emulated_noalloc */
 
-/* Reducer variants (section 3.1, "ScaLAPACK style" / "ELPA style"). */
+/* Reducer variants (section 3.1, "ScaLAPACK style" / "ELPA style" / "EigenExa style"). */
 #define GEP_RED_TWOSIDED 0     /* C = L^-1 A L^-T by triangular solves, L^-1 never formed */
 #define GEP_RED_EXPLICIT_INV 1 /* R = L^-1 formed explicitly, then C = R A R^T           */
+#define GEP_RED_EIGENEXA 2     /* Cholesky-free (Eq. 7-9): B W = W D by the SEP solver,
+                                  C = A' = D^-1/2 W^T A W D^-1/2, Y = W D^-1/2 Z          */
 
 /* SEP-solver variants (section 3.1: conventional tridiagonalisation, or
  * narrow-band reduction followed by band -> tridiagonal). */
@@ -72,9 +74,20 @@ typedef struct gep_options {
   int overwrite;    /* 1: A and B may be destroyed by gep_solve (saves two copies) */
   int timers;       /* 1: record per-stage CUDA-event times (gep_get_stage_times) */
   int refine_iters; /* GEP_PREC_MIXED_REFINED: FP64 refinement steps; 0 = until converged */
+  int n_want;       /* 0: all M eigenpairs; 1..M: only the n_want lowest (section 2: the occupied
+                       states), w[0..n_want) and Y M x n_want.  Eigenvalues only: bisection for
+                       those indices; with vectors: divide and conquer gives every eigenvector of
+                       T, and only the n_want wanted columns are back-transformed (Q2, Q1, Eq. 6
+                       or Eq. 9 on n_want columns).  Not with GEP_PREC_MIXED_REFINED nor in
+                       gep_solve_batched (GEP_ERR_UNSUPPORTED). */
 } gep_options;
 
 /* Fills *o with the defaults: TWOSIDED, 1STAGE, b = 0, FP64, vectors, no overwrite, no timers.
+ * GEP_RED_EIGENEXA runs the SEP solver twice with the same options (sep, bandwidth, precision):
+ * first on B with eigenvectors (Eq. 7), then on A' (Eq. 8); the stage times of
+ * gep_get_stage_times then read t[0] = SEP of B (Eq. 7), t[1] = forming A' (Eq. 8),
+ * t[5] = Y = W D^-1/2 Z (Eq. 9).  If B has k > 0 eigenvalues that are not positive,
+ * gep_get_info reports k and the later stages become no-ops.
  * GEP_PREC_MIXED_REFINED (needs want_vectors = 1): every dense product of the solve runs
  * on the FP32-grade split-BF16 engine and the SYMVs in FP32; FP64 stays in the diagonal
  * blocks, the secular equations and deflation; then all eigenpairs are refined in FP64
@@ -109,7 +122,12 @@ int gep_set_workspace(gep_handle_t h, void* dptr, size_t bytes);
  *   variant GEP_RED_EXPLICIT_INV additionally overwrites B's lower triangle with
  *   R = L^-1 (ELPA style "R2"), which gep_backtransform then multiplies by.
  * gep_backtransform: Eq. 6.  Z (M x ncol) is overwritten by Y = L^-T Z
- *   (variant TWOSIDED: triangular solve with L in B) or Y = R^T Z (EXPLICIT_INV). */
+ *   (variant TWOSIDED: triangular solve with L in B) or Y = R^T Z (EXPLICIT_INV).
+ * Variant GEP_RED_EIGENEXA (Eq. 7-9, no Cholesky factor): gep_reduce takes the original B
+ *   (lower triangle read; do not call gep_cholesky first), solves B W = W D with the 1-stage
+ *   SEP solver and overwrites B (all M x M entries) with X = W D^-1/2 and A (both triangles)
+ *   with A' = X^T A X; status k > 0 when k eigenvalues of B are not positive.
+ *   gep_backtransform then forms Y = X Z with X in B. */
 int gep_cholesky(gep_handle_t h, int M, double* B, int ldb);
 int gep_reduce(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, int variant);
 int gep_backtransform(gep_handle_t h, int M, int ncol, const double* B, int ldb, double* Z, int ldz,
@@ -154,10 +172,11 @@ int sep_backtransform_2stage(gep_handle_t h, int M, int ncol, int b, const doubl
                              const double* tau1, const double* q2, double* Z, int ldz);
 
 /* ---- whole workflow ------------------------------------------------------------
- * gep_solve: Eq. 2 for all M eigenpairs.  A, B (lower) are read and preserved unless
- *   o->overwrite.  w[M] receives eigenvalues ascending; if o->want_vectors, Y (M x M,
- *   ldy) receives B-orthonormal eigenvectors whose largest-magnitude entry is positive
- *   (ties: lowest row index).  Uses the workspace set with gep_set_workspace. */
+ * gep_solve: Eq. 2 for all M eigenpairs (or the n = o->n_want lowest).  A, B (lower) are
+ *   read and preserved unless o->overwrite.  w[n] receives eigenvalues ascending; if
+ *   o->want_vectors, Y (M x n, ldy) receives B-orthonormal eigenvectors whose
+ *   largest-magnitude entry is positive (ties: lowest row index).  Uses the workspace set
+ *   with gep_set_workspace.  Returns -10 for o == NULL or o->n_want outside [0, M]. */
 int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, double* w, double* Y,
               int ldy, const gep_options* o);
 

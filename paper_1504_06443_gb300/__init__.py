@@ -19,20 +19,20 @@ import threading
 
 __all__ = ["load", "solve", "solve_host", "cholesky", "reduce", "tridiag_1stage", "tridiag_eig",
            "sep_backtransform", "tridiag_2stage", "sep_backtransform_2stage", "gep_backtransform", "dgemm", "Handle", "default_handle",
-           "RED_TWOSIDED", "RED_EXPLICIT_INV", "SEP_1STAGE", "SEP_2STAGE", "PREC_FP64",
+           "RED_TWOSIDED", "RED_EXPLICIT_INV", "RED_EIGENEXA", "SEP_1STAGE", "SEP_2STAGE", "PREC_FP64",
            "PREC_FP64_EMULATED", "PREC_MIXED_REFINED", "GepError", "shard_batch"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libgep.so")
 
-RED_TWOSIDED, RED_EXPLICIT_INV = 0, 1
+RED_TWOSIDED, RED_EXPLICIT_INV, RED_EIGENEXA = 0, 1, 2
 SEP_1STAGE, SEP_2STAGE = 0, 1
 PREC_FP64, PREC_FP64_EMULATED, PREC_MIXED_REFINED = 0, 1, 2
 # return codes of include/gep.h
 ERR_CUDA, ERR_ALLOC, ERR_NONFINITE, ERR_TIMEOUT, ERR_HANDLE, ERR_UNSUPPORTED, ERR_TOO_LARGE = (
     -100, -101, -102, -103, -104, -105, -106)
 
-_REDUCERS = {"twosided": RED_TWOSIDED, "explicit_inv": RED_EXPLICIT_INV}
+_REDUCERS = {"twosided": RED_TWOSIDED, "explicit_inv": RED_EXPLICIT_INV, "eigenexa": RED_EIGENEXA}
 _SEPS = {"1stage": SEP_1STAGE, "2stage": SEP_2STAGE}
 _PRECS = {"fp64": PREC_FP64, "fp64_emulated": PREC_FP64_EMULATED, "mixed_refined": PREC_MIXED_REFINED}
 
@@ -47,7 +47,7 @@ class GepError(RuntimeError):
 class GepOptions(ctypes.Structure):
     _fields_ = [("reducer", ctypes.c_int), ("sep", ctypes.c_int), ("bandwidth", ctypes.c_int),
                 ("precision", ctypes.c_int), ("want_vectors", ctypes.c_int), ("overwrite", ctypes.c_int),
-                ("timers", ctypes.c_int), ("refine_iters", ctypes.c_int)]
+                ("timers", ctypes.c_int), ("refine_iters", ctypes.c_int), ("n_want", ctypes.c_int)]
 
 
 _lib = None
@@ -316,7 +316,7 @@ def default_handle():
 
 
 def make_options(reducer="twosided", sep="1stage", precision="fp64", want_vectors=True, overwrite=False,
-                 timers=False, bandwidth=0, refine_iters=0):
+                 timers=False, bandwidth=0, refine_iters=0, n_want=0):
     o = GepOptions()
     load().gep_default_options(ctypes.byref(o))
     o.reducer = _REDUCERS[reducer] if isinstance(reducer, str) else int(reducer)
@@ -327,6 +327,7 @@ def make_options(reducer="twosided", sep="1stage", precision="fp64", want_vector
     o.timers = 1 if timers else 0
     o.bandwidth = int(bandwidth)
     o.refine_iters = int(refine_iters)
+    o.n_want = int(n_want)
     return o
 
 
@@ -339,35 +340,40 @@ def workspace_bytes(M, handle=None, **opts):
 
 
 def solve(A, B, reducer="twosided", sep="1stage", precision="fp64", want_vectors=True, overwrite=False,
-          timers=False, bandwidth=0, handle=None, out=None, refine_iters=0):
-    """All eigenpairs of A y = lambda B y (A, B symmetric float64 CUDA tensors, B SPD).
+          timers=False, bandwidth=0, handle=None, out=None, refine_iters=0, n_want=0):
+    """All eigenpairs of A y = lambda B y (A, B symmetric float64 CUDA tensors, B SPD), or
+    only the n_want lowest (0 = all).
 
-    Returns (w, Y, info): w ascending, Y (column-major view) B-orthonormal or None.
-    info != 0 reports a numerical failure (k: B's leading minor k not positive definite)."""
+    Returns (w, Y, info): w ascending (n entries), Y (M x n column-major view) B-orthonormal
+    or None.  info != 0 reports a numerical failure (k: B's leading minor k not positive
+    definite)."""
     torch = _torch()
     _need_matrix(A, "A", square=True, f64=True, cuda=False)
     M = int(A.shape[0])
     _need_matrix(B, "B", rows=M, cols=M, f64=True, cuda=False)
+    if not 0 <= int(n_want) <= M:
+        raise ValueError(f"n_want must lie in [0, {M}]")
+    n = int(n_want) if n_want else M
     if out is not None:
-        _need_vector(out[0], "out[0] (w)", M, f64=True)
+        _need_vector(out[0], "out[0] (w)", n, f64=True)
         if want_vectors:
-            _need_matrix(out[1], "out[1] (Y^T)", rows=M, cols=M, f64=True)
+            _need_matrix(out[1], "out[1] (Y^T)", rows=n, cols=M, f64=True)
             if not out[1].is_contiguous():
                 raise ValueError("out[1] (Y^T) must be contiguous")
     _need_on_device("A", A, "B", B)
     h = handle or default_handle()
     _same_device(h, A, B)
-    o = make_options(reducer, sep, precision, want_vectors, overwrite, timers, bandwidth, refine_iters)
-    n = _SZ()
-    _check(h.lib.gep_workspace_size(h.h, M, ctypes.byref(o), ctypes.byref(n)), "gep_workspace_size")
-    h.ensure_workspace(n.value)
+    o = make_options(reducer, sep, precision, want_vectors, overwrite, timers, bandwidth, refine_iters, n_want)
+    nb = _SZ()
+    _check(h.lib.gep_workspace_size(h.h, M, ctypes.byref(o), ctypes.byref(nb)), "gep_workspace_size")
+    h.ensure_workspace(nb.value)
     pa, lda = _sym_ptr_ld(A)
     pb, ldb = _sym_ptr_ld(B)
     if out is not None:
         w, Yt = out
     else:
-        w = torch.empty(M, dtype=torch.float64, device=A.device)
-        Yt = torch.empty((M, M), dtype=torch.float64, device=A.device) if want_vectors else None
+        w = torch.empty(n, dtype=torch.float64, device=A.device)
+        Yt = torch.empty((n, M), dtype=torch.float64, device=A.device) if want_vectors else None
     _check(h.lib.gep_solve(h.h, M, pa, lda, pb, ldb, _ptr(w), _ptr(Yt), max(1, M), ctypes.byref(o)), "gep_solve")
     info = h.info()
     return w, (Yt.t() if Yt is not None else None), info
@@ -388,18 +394,19 @@ def solve_async(A, B, w, Yt, opts, handle):
 
 
 def solve_host(A_np, B_np, want_vectors=True, handle=None, **opts):
-    """Host numpy arrays in and out (copies inside the library).  Returns (w, Y)."""
+    """Host numpy arrays in and out (copies inside the library).  Returns (w, Y, info)."""
     import numpy as np
     h = handle or default_handle()
     M = int(A_np.shape[0])
     o = make_options(want_vectors=want_vectors, **opts)
-    n = _SZ()
-    _check(h.lib.gep_workspace_size_host(h.h, M, ctypes.byref(o), ctypes.byref(n)), "gep_workspace_size_host")
-    h.ensure_workspace(n.value)
+    nk = o.n_want if o.n_want else M
+    nb = _SZ()
+    _check(h.lib.gep_workspace_size_host(h.h, M, ctypes.byref(o), ctypes.byref(nb)), "gep_workspace_size_host")
+    h.ensure_workspace(nb.value)
     A = np.ascontiguousarray(A_np, dtype=np.float64)
     B = np.ascontiguousarray(B_np, dtype=np.float64)
-    w = np.empty(M)
-    Y = np.empty((M, M), order="F") if want_vectors else None
+    w = np.empty(nk)
+    Y = np.empty((M, nk), order="F") if want_vectors else None
     _check(h.lib.gep_solve_host(h.h, M, A.ctypes.data_as(_P), max(1, M), B.ctypes.data_as(_P), max(1, M),
                                 w.ctypes.data_as(_P), Y.ctypes.data_as(_P) if Y is not None else None,
                                 max(1, M), ctypes.byref(o)), "gep_solve_host")
@@ -430,7 +437,9 @@ def _stage_ws(M, ncol=None, handle=None):
 
 
 def reduce(A, L, variant="twosided", handle=None):
-    """Eq. 5: (C, L_or_R).  For 'explicit_inv' the returned second matrix is R = L^-1."""
+    """Eq. 5: (C, L_or_R).  For 'explicit_inv' the returned second matrix is R = L^-1.
+    For 'eigenexa' (Eq. 7-8, no Cholesky factor) pass B itself as L: the result is
+    (A' = X^T A X, X = W D^-1/2) with B W = W D."""
     _need_matrix(A, "A", square=True, cuda=False)
     _need_matrix(L, "L", rows=A.shape[0], cols=A.shape[0], cuda=False)
     _need_on_device("A", A, "L", L)
@@ -444,7 +453,7 @@ def reduce(A, L, variant="twosided", handle=None):
 
 
 def gep_backtransform(LR, Z, variant="twosided", handle=None):
-    """Eq. 6: Y = L^-T Z (twosided) or Y = R^T Z (explicit_inv)."""
+    """Eq. 6: Y = L^-T Z (twosided) or Y = R^T Z (explicit_inv); Eq. 9: Y = X Z (eigenexa)."""
     _need_matrix(LR, "LR", square=True, cuda=False)
     _need_matrix(Z, "Z", rows=LR.shape[0], cuda=False)
     _need_on_device("LR", LR, "Z", Z)

@@ -15,7 +15,7 @@ constexpr int NB = 128;  // diagonal block order of the triangular kernels (tri.
 bool handle_ok(gep_handle_t h) { return h != nullptr && h->magic == 0x6e70; }
 
 struct SolveLayout {
-  size_t Cw, Lw, invD, vec, uni, eng, af, q2, end;  // byte offsets
+  size_t Cw, Lw, invD, vec, uni, eng, af, q2, xw, zt, end;  // byte offsets
   size_t uni_bytes, eng_bytes;
 };
 
@@ -23,6 +23,12 @@ constexpr int kDefaultBand = 64;  // bandwidth of the two-stage reduction when o
 
 int band_of(const gep_options* o) { return o->bandwidth > 0 ? o->bandwidth : kDefaultBand; }
 bool two_stage(const gep_options* o) { return o->sep == GEP_SEP_2STAGE; }
+bool eigenexa(const gep_options* o) { return o->reducer == GEP_RED_EIGENEXA; }
+// the SEP solver runs with eigenvectors: for the caller's pencil, or on B (Eq. 7)
+bool sep_vectors(const gep_options* o) { return o->want_vectors || eigenexa(o); }
+// only the lowest n_want eigenpairs, with vectors: D&C writes all eigenvectors of T to a
+// workspace matrix first
+bool partial_vectors(int M, const gep_options* o) { return o->want_vectors && o->n_want > 0 && o->n_want < M; }
 
 size_t r256(size_t x) { return align256(x); }
 
@@ -34,15 +40,19 @@ size_t invd_bytes(int M) {
 size_t union_bytes(int M, const gep_options* o) {
   size_t mm = (size_t)M * M * sizeof(double);
   size_t tmpb = (size_t)NB * M * sizeof(double);
-  size_t red = (o->reducer == GEP_RED_EXPLICIT_INV) ? r256(mm) + r256(mm) + r256(tmpb) : r256(mm) + r256(tmpb);
+  size_t red = (o->reducer == GEP_RED_EXPLICIT_INV) ? r256(mm) + r256(mm) + r256(tmpb)
+               : eigenexa(o) ? r256(mm)  // A X of Eq. 8
+                             : r256(mm) + r256(tmpb);
   size_t tri = two_stage(o) ? band_ws_elems(M, band_of(o)) * sizeof(double) : tridiag_ws_elems(M) * sizeof(double);
-  size_t dc = o->want_vectors ? dc_ws_bytes(M) : 0;
-  size_t bt = o->want_vectors ? backtransform_ws_elems(M, M) * sizeof(double) : 0;
-  if (two_stage(o) && o->want_vectors) {
+  size_t dc = sep_vectors(o) ? dc_ws_bytes(M) : 0;
+  size_t bt = sep_vectors(o) ? backtransform_ws_elems(M, M) * sizeof(double) : 0;
+  if (two_stage(o) && sep_vectors(o)) {
     size_t q2t = q2_tile_ws_elems(M, band_of(o)) * sizeof(double);
     if (q2t > bt) bt = q2t;
   }
-  size_t r3 = o->want_vectors ? (r256(tmpb) + (o->reducer == GEP_RED_EXPLICIT_INV ? r256(mm) : 0)) : 0;
+  size_t r3 = (o->want_vectors && !eigenexa(o))
+                  ? (r256(tmpb) + (o->reducer == GEP_RED_EXPLICIT_INV ? r256(mm) : 0))
+                  : 0;
   size_t rf = (o->precision == GEP_PREC_MIXED_REFINED) ? r256(refine_ws_elems(M) * sizeof(double)) : 0;
   size_t u = red;
   if (rf > u) u = rf;
@@ -60,7 +70,7 @@ SolveLayout layout(int M, const gep_options* o) {
   L.Cw = off; off += o->overwrite ? 0 : r256(mm);
   L.Lw = off; off += o->overwrite ? 0 : r256(mm);
   L.invD = off; off += r256(invd_bytes(M));
-  L.vec = off; off += r256((size_t)3 * (M + 1) * sizeof(double));
+  L.vec = off; off += r256((size_t)5 * (M + 1) * sizeof(double));
   L.uni = off;
   L.uni_bytes = union_bytes(M, o);
   off += L.uni_bytes;
@@ -70,14 +80,19 @@ SolveLayout layout(int M, const gep_options* o) {
   L.af = off;  // full symmetric A and B kept for the FP64 refinement
   off += (o->precision == GEP_PREC_MIXED_REFINED) ? 2 * r256(mm) : 0;
   L.q2 = off;  // bulge-chasing reflectors, kept from S1c to the back-transformation
-  off += (two_stage(o) && o->want_vectors) ? r256(q2_elems(M, band_of(o)) * sizeof(double)) : 0;
+  off += (two_stage(o) && sep_vectors(o)) ? r256(q2_elems(M, band_of(o)) * sizeof(double)) : 0;
+  L.xw = off;  // X = W D^-1/2 of the Cholesky-free reducer (Eq. 7-9)
+  off += eigenexa(o) ? r256(mm) : 0;
+  L.zt = off;  // all eigenvectors of T when only the lowest n_want are back-transformed
+  off += partial_vectors(M, o) ? r256(mm) : 0;
   L.end = off;
   return L;
 }
 
 int check_opts(const gep_options* o) {
   if (!o) return -1;
-  if (o->reducer != GEP_RED_TWOSIDED && o->reducer != GEP_RED_EXPLICIT_INV) return GEP_ERR_UNSUPPORTED;
+  if (o->reducer != GEP_RED_TWOSIDED && o->reducer != GEP_RED_EXPLICIT_INV && o->reducer != GEP_RED_EIGENEXA)
+    return GEP_ERR_UNSUPPORTED;
   if (o->sep != GEP_SEP_1STAGE && o->sep != GEP_SEP_2STAGE) return GEP_ERR_UNSUPPORTED;
   if (o->sep == GEP_SEP_2STAGE && (o->bandwidth < 0 || o->bandwidth > 64)) return GEP_ERR_UNSUPPORTED;
   if (o->precision != GEP_PREC_FP64 && o->precision != GEP_PREC_FP64_EMULATED &&
@@ -85,6 +100,8 @@ int check_opts(const gep_options* o) {
     return GEP_ERR_UNSUPPORTED;
   if (o->precision == GEP_PREC_MIXED_REFINED && !o->want_vectors) return GEP_ERR_UNSUPPORTED;
   if (o->refine_iters < 0) return -10;
+  if (o->n_want < 0) return -10;
+  if (o->n_want > 0 && o->precision == GEP_PREC_MIXED_REFINED) return GEP_ERR_UNSUPPORTED;
   return GEP_OK;
 }
 
@@ -95,6 +112,48 @@ int reset_status(gep_handle_t h) {
 
 void mark(gep_handle_t h, const gep_options* o, int i) {
   if (o->timers) cudaEventRecord(h->ev[i], h->stream);
+}
+
+// SEP solver of section 3.1 (a) on the symmetric C (lower triangle read, overwritten by the
+// reflectors): tridiagonalisation (1-stage, or full -> band -> tridiagonal), then either the
+// eigenvalues w by bisection (Z == nullptr) or divide and conquer with the eigenvectors of T
+// written to Z and back-transformed.  n < M: only the n lowest eigenpairs (w[0..n), Z M x n);
+// with vectors D&C then writes all eigenvalues to wt and all eigenvectors of T to Zt (M x M)
+// and only the first n columns are copied to Z and back-transformed.  timed: record marks 3
+// (after TRD/BAND) and 4 (after D&C) and the S1b/S1c split of the caller's timers.
+int sep_solve(gep_handle_t h, int M, double* C, int ldc, const gep_options* o, double* dvec, double* evec,
+              double* tvec, double* q2, char* uni, size_t uni_bytes, int eng, double* w, double* Z, int ldz,
+              bool timed, int n = 0, double* Zt = nullptr, double* wt = nullptr) {
+  if (n <= 0 || n > M) n = M;
+  const int bw = band_of(o);
+  if (two_stage(o)) {
+    GEP_CHECK(band_reduce(h, M, C, ldc, bw, tvec, (double*)uni, uni_bytes / sizeof(double), eng));  // S1b
+    if (timed && o->timers) cudaEventRecord(h->ev_band, h->stream);
+    GEP_CHECK(band_to_tridiag(h, M, C, ldc, bw, dvec, evec, Z ? q2 : nullptr, (double*)uni,
+                              uni_bytes / sizeof(double)));  // S1c
+  } else {
+    GEP_CHECK(tridiag_1stage(h, M, C, ldc, dvec, evec, tvec, (double*)uni, uni_bytes / sizeof(double), eng));
+  }
+  if (timed) mark(h, o, 3);
+  if (!Z) {
+    GEP_CHECK(tridiag_eig_bisect(h, M, dvec, evec, w, n));
+    if (timed) mark(h, o, 4);
+    return GEP_OK;
+  }
+  if (n < M) {
+    if (!Zt || !wt) return GEP_ERR_ALLOC;
+    GEP_CHECK(tridiag_eig_dc(h, M, dvec, evec, wt, Zt, M, (double*)uni, uni_bytes, eng));  // D&C
+    GEP_CHECK(copy_matrix(h, n, 1, wt, n, w, n));
+    GEP_CHECK(copy_matrix(h, M, n, Zt, M, Z, ldz));  // the n lowest eigenvectors of T
+  } else {
+    GEP_CHECK(tridiag_eig_dc(h, M, dvec, evec, w, Z, ldz, (double*)uni, uni_bytes, eng));  // D&C
+  }
+  if (timed) mark(h, o, 4);
+  if (two_stage(o)) {
+    GEP_CHECK(apply_q2(h, M, bw, q2, Z, ldz, n, eng, (double*)uni, uni_bytes / sizeof(double)));
+    return backtransform_q(h, M, n, C, ldc, tvec, Z, ldz, (double*)uni, uni_bytes / sizeof(double), eng, bw);
+  }
+  return backtransform_q(h, M, n, C, ldc, tvec, Z, ldz, (double*)uni, uni_bytes / sizeof(double), eng);
 }
 
 }  // namespace
@@ -180,7 +239,14 @@ int gep_stage_workspace_size(gep_handle_t h, int M, int ncol, size_t* bytes) {
   size_t dc = dc_ws_bytes(M);
   size_t bt = d * backtransform_ws_elems(M, ncol > 0 ? ncol : 1);
   size_t band = d * band_ws_elems(M, 64);                                              // largest bandwidth
-  for (size_t x : {red, bks, tri, dc, bt, band})
+  // gep_reduce, Cholesky-free variant: copy of B, four vectors, then the largest SEP stage
+  size_t sep_max = tri;
+  for (size_t x : {dc, d * backtransform_ws_elems(M, M), d * mm})
+    if (x > sep_max) sep_max = x;
+  size_t ee = d * mm + d * 4 * ((size_t)M + 1) + sep_max;
+  size_t bke = d * mm;  // gep_backtransform, Cholesky-free variant: X Z
+  if (ncol > M) bke = d * (size_t)M * ncol;
+  for (size_t x : {red, bks, tri, dc, bt, band, ee, bke})
     if (x > need) need = x;
   *bytes = need + slack;
   return GEP_OK;
@@ -386,9 +452,31 @@ int gep_reduce(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, in
   if (lda < (M > 1 ? M : 1)) return -4;
   if (M > 0 && !B) return -5;
   if (ldb < (M > 1 ? M : 1)) return -6;
-  if (variant != GEP_RED_TWOSIDED && variant != GEP_RED_EXPLICIT_INV) return -7;
+  if (variant != GEP_RED_TWOSIDED && variant != GEP_RED_EXPLICIT_INV && variant != GEP_RED_EIGENEXA) return -7;
   if (M == 0) return GEP_OK;
   Arena ar(h->ws, h->ws_bytes);
+  if (variant == GEP_RED_EIGENEXA) {
+    // Eq. 7 with the 1-stage SEP solver: S = copy of B -> reflectors, W into B, X = W D^-1/2
+    double* S = ar.take<double>((size_t)M * M);
+    double* v = ar.take<double>((size_t)4 * (M + 1));
+    const size_t mm = (size_t)M * M;
+    size_t n = tridiag_ws_elems(M);
+    if (dc_ws_bytes(M) / sizeof(double) + 1 > n) n = dc_ws_bytes(M) / sizeof(double) + 1;
+    if (backtransform_ws_elems(M, M) > n) n = backtransform_ws_elems(M, M);
+    if (mm > n) n = mm;
+    double* ws = ar.take<double>(n);
+    if (!ar.ok) return GEP_ERR_ALLOC;
+    double *dv = v, *ev = v + (M + 1), *tv = v + 2 * (M + 1), *wB = v + 3 * (M + 1);
+    GEP_CHECK(copy_lower(h, M, B, ldb, S, M));
+    GEP_CHECK(tridiag_1stage(h, M, S, M, dv, ev, tv, ws, n, GEP_PREC_FP64));
+    GEP_CHECK(tridiag_eig_dc(h, M, dv, ev, wB, B, ldb, ws, n * sizeof(double), GEP_PREC_FP64));
+    GEP_CHECK(backtransform_q(h, M, M, S, M, tv, B, ldb, ws, n, GEP_PREC_FP64));
+    GEP_CHECK(scale_cols_rsqrt_checked(h, M, M, wB, B, ldb));
+    // Eq. 8: A' = X^T (A X) into A (both triangles)
+    GEP_CHECK(dgemm(h, 'S', 'N', 'F', M, M, M, 1.0, A, lda, B, ldb, 0.0, ws, M, GEP_PREC_FP64));
+    GEP_CHECK(dgemm(h, 'T', 'N', 'L', M, M, M, 1.0, B, ldb, ws, M, 0.0, A, lda, GEP_PREC_FP64));
+    return symmetrize_lower(h, M, A, lda);
+  }
   double* invD = ar.take<double>(invd_bytes(M) / sizeof(double));
   double* X = ar.take<double>((size_t)M * M);
   double* tmp = ar.take<double>((size_t)M * M + (size_t)NB * M);
@@ -407,9 +495,15 @@ int gep_backtransform(gep_handle_t h, int M, int ncol, const double* B, int ldb,
   if (ldb < (M > 1 ? M : 1)) return -5;
   if (M > 0 && ncol > 0 && !Z) return -6;
   if (ldz < (M > 1 ? M : 1)) return -7;
-  if (variant != GEP_RED_TWOSIDED && variant != GEP_RED_EXPLICIT_INV) return -8;
+  if (variant != GEP_RED_TWOSIDED && variant != GEP_RED_EXPLICIT_INV && variant != GEP_RED_EIGENEXA) return -8;
   if (M == 0 || ncol == 0) return GEP_OK;
   Arena ar(h->ws, h->ws_bytes);
+  if (variant == GEP_RED_EIGENEXA) {  // Eq. 9: Y = X Z with X = W D^-1/2 in B (full)
+    double* T = ar.take<double>((size_t)M * ncol);
+    if (!ar.ok) return GEP_ERR_ALLOC;
+    GEP_CHECK(dgemm(h, 'N', 'N', 'F', M, ncol, M, 1.0, B, ldb, Z, ldz, 0.0, T, M, GEP_PREC_FP64));
+    return copy_matrix(h, M, ncol, T, M, Z, ldz);
+  }
   if (variant == GEP_RED_TWOSIDED) {
     double* invD = ar.take<double>(invd_bytes(M) / sizeof(double));
     double* tmp = ar.take<double>((size_t)NB * ncol);
@@ -534,10 +628,12 @@ int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, dou
   if (ldb < (M > 1 ? M : 1)) return -6;
   if (M > 0 && !w) return -7;
   if (!o) return -10;
+  if (o->n_want < 0 || o->n_want > M) return -10;
   if (o->want_vectors && M > 0 && !Y) return -8;
   if (o->want_vectors && ldy < (M > 1 ? M : 1)) return -9;
   GEP_CHECK(check_opts(o));
   if (M == 0) return GEP_OK;
+  const int n = o->n_want > 0 ? o->n_want : M;  // eigenpairs wanted (the lowest n)
   SolveLayout Ly = layout(M, o);
   if (h->ws == nullptr || h->ws_bytes < Ly.end) return GEP_ERR_ALLOC;
   const int eng = o->precision;
@@ -571,64 +667,75 @@ int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, dou
     GEP_CHECK(copy_lower(h, M, A, lda, Cw, ldcw));
     GEP_CHECK(copy_lower(h, M, B, ldb, Lw, ldlw));
   }
-  mark(h, o, 0);
-  GEP_CHECK(cholesky(h, M, Lw, ldlw, invD, eng));  // R1
-  mark(h, o, 1);
-  {
-    double* X = (double*)uni;
-    double* tmp = (double*)(uni + r256((size_t)M * M * sizeof(double)));
-    if (o->reducer == GEP_RED_TWOSIDED)
-      GEP_CHECK(reduce_twosided(h, M, Cw, ldcw, Lw, ldlw, invD, X, tmp, eng));  // R2
-    else {
-      GEP_CHECK(reduce_explicit_inv(h, M, Cw, ldcw, Lw, ldlw, invD, X, tmp, eng));
-      GEP_CHECK(zero_upper(h, M, Lw, ldlw));  // R is used as a full matrix by Eq. 6 below
-    }
-  }
-  mark(h, o, 2);
-  const int bw = band_of(o);
+  double* wB = tvec + (M + 1);  // eigenvalues D of B (Cholesky-free reducer)
+  double* wT = wB + (M + 1);     // all eigenvalues of T when only the lowest n are wanted
+  double* Zt = partial_vectors(M, o) ? (double*)(base + Ly.zt) : nullptr;
   h->band_recorded = two_stage(o) && o->timers;
-  double* q2 = (two_stage(o) && o->want_vectors) ? (double*)(base + Ly.q2) : nullptr;
-  if (two_stage(o)) {
-    GEP_CHECK(band_reduce(h, M, Cw, ldcw, bw, tvec, (double*)uni, Ly.uni_bytes / sizeof(double), eng));   // S1b
-    if (o->timers) cudaEventRecord(h->ev_band, h->stream);
-    GEP_CHECK(band_to_tridiag(h, M, Cw, ldcw, bw, dvec, evec, q2, (double*)uni,
-                              Ly.uni_bytes / sizeof(double)));  // S1c
-  } else {
-    GEP_CHECK(tridiag_1stage(h, M, Cw, ldcw, dvec, evec, tvec, (double*)uni, Ly.uni_bytes / sizeof(double), eng));
-  }
-  mark(h, o, 3);
-  if (!o->want_vectors) {
-    GEP_CHECK(tridiag_eig_bisect(h, M, dvec, evec, w));
-    mark(h, o, 4);
-    mark(h, o, 5);
-    mark(h, o, 6);
-    mark(h, o, 7);
-    h->timers_recorded = o->timers != 0;
-    return GEP_OK;
-  }
-  GEP_CHECK(tridiag_eig_dc(h, M, dvec, evec, w, Y, ldy, (double*)uni, Ly.uni_bytes, eng));  // D&C
-  mark(h, o, 4);
-  if (two_stage(o)) {
-    GEP_CHECK(apply_q2(h, M, bw, q2, Y, ldy, M, eng, (double*)uni, Ly.uni_bytes / sizeof(double)));
-    GEP_CHECK(backtransform_q(h, M, M, Cw, ldcw, tvec, Y, ldy, (double*)uni, Ly.uni_bytes / sizeof(double), eng,
-                              bw));
-  } else {
-    GEP_CHECK(backtransform_q(h, M, M, Cw, ldcw, tvec, Y, ldy, (double*)uni, Ly.uni_bytes / sizeof(double), eng));
-  }
-  mark(h, o, 5);
-  if (o->reducer == GEP_RED_TWOSIDED) {
-    GEP_CHECK(trsm_llt(h, M, M, Lw, ldlw, invD, NB, Y, ldy, (double*)uni, eng));  // Eq. 6
-  } else {
+  double* q2 = (two_stage(o) && sep_vectors(o)) ? (double*)(base + Ly.q2) : nullptr;
+  mark(h, o, 0);
+  if (eigenexa(o)) {
+    // Eq. 7: B W = W D by the SEP solver (B's copy becomes its reflectors), X = W D^-1/2
+    double* Xw = (double*)(base + Ly.xw);
+    GEP_CHECK(sep_solve(h, M, Lw, ldlw, o, dvec, evec, tvec, q2, uni, Ly.uni_bytes, eng, wB, Xw, M, false));
+    GEP_CHECK(scale_cols_rsqrt_checked(h, M, M, wB, Xw, M));  // status k: k eigenvalues of B <= 0
+    mark(h, o, 1);
+    // Eq. 8: A' = X^T (A X), lower triangle (all the SEP solver reads)
     double* T = (double*)uni;
-    GEP_CHECK(dgemm(h, 'T', 'N', 'F', M, M, M, 1.0, Lw, ldlw, Y, ldy, 0.0, T, M, eng));  // Y = R^T Z
-    GEP_CHECK(copy_matrix(h, M, M, T, M, Y, ldy));
+    GEP_CHECK(dgemm(h, 'S', 'N', 'F', M, M, M, 1.0, Cw, ldcw, Xw, M, 0.0, T, M, eng));
+    GEP_CHECK(dgemm(h, 'T', 'N', 'L', M, M, M, 1.0, Xw, M, T, M, 0.0, Cw, ldcw, eng));
+    mark(h, o, 2);
+    // A' Z = Z Lambda (Z into B's buffer, no longer needed), then Eq. 9: Y = X Z
+    double* Z = o->want_vectors ? Lw : nullptr;
+    GEP_CHECK(sep_solve(h, M, Cw, ldcw, o, dvec, evec, tvec, q2, uni, Ly.uni_bytes, eng, w, Z, ldlw, true, n, Zt,
+                        wT));
+    if (!o->want_vectors) {
+      mark(h, o, 5);
+      mark(h, o, 6);
+      mark(h, o, 7);
+      h->timers_recorded = o->timers != 0;
+      return GEP_OK;
+    }
+    mark(h, o, 5);
+    GEP_CHECK(dgemm(h, 'N', 'N', 'F', M, n, M, 1.0, Xw, M, Z, ldlw, 0.0, Y, ldy, eng));
+    mark(h, o, 6);
+  } else {
+    GEP_CHECK(cholesky(h, M, Lw, ldlw, invD, eng));  // R1
+    mark(h, o, 1);
+    {
+      double* X = (double*)uni;
+      double* tmp = (double*)(uni + r256((size_t)M * M * sizeof(double)));
+      if (o->reducer == GEP_RED_TWOSIDED)
+        GEP_CHECK(reduce_twosided(h, M, Cw, ldcw, Lw, ldlw, invD, X, tmp, eng));  // R2
+      else {
+        GEP_CHECK(reduce_explicit_inv(h, M, Cw, ldcw, Lw, ldlw, invD, X, tmp, eng));
+        GEP_CHECK(zero_upper(h, M, Lw, ldlw));  // R is used as a full matrix by Eq. 6 below
+      }
+    }
+    mark(h, o, 2);
+    GEP_CHECK(sep_solve(h, M, Cw, ldcw, o, dvec, evec, tvec, q2, uni, Ly.uni_bytes, eng, w,
+                        o->want_vectors ? Y : nullptr, ldy, true, n, Zt, wT));
+    if (!o->want_vectors) {
+      mark(h, o, 5);
+      mark(h, o, 6);
+      mark(h, o, 7);
+      h->timers_recorded = o->timers != 0;
+      return GEP_OK;
+    }
+    mark(h, o, 5);
+    if (o->reducer == GEP_RED_TWOSIDED) {
+      GEP_CHECK(trsm_llt(h, M, n, Lw, ldlw, invD, NB, Y, ldy, (double*)uni, eng));  // Eq. 6
+    } else {
+      double* T = (double*)uni;
+      GEP_CHECK(dgemm(h, 'T', 'N', 'F', M, n, M, 1.0, Lw, ldlw, Y, ldy, 0.0, T, M, eng));  // Y = R^T Z
+      GEP_CHECK(copy_matrix(h, M, n, T, M, Y, ldy));
+    }
+    mark(h, o, 6);
   }
-  mark(h, o, 6);
   if (mixed) {
     GEP_CHECK(refine_eigenpairs(h, M, Af, Bf, Y, ldy, w, (double*)uni, o->refine_iters, GEP_PREC_FP64_EMULATED));
   }
   mark(h, o, 7);
-  GEP_CHECK(sign_convention(h, M, M, Y, ldy));
+  GEP_CHECK(sign_convention(h, M, n, Y, ldy));
   h->timers_recorded = o->timers != 0;
   return GEP_OK;
 }
@@ -730,6 +837,7 @@ int gep_solve_batched(gep_handle_t h, int count, const int* M, double* const* A,
   if (count > 0 && (!M || !A || !B || !w || !Y)) return -3;
   if (!o) return -8;
   if (nstreams < 1 || nstreams > 64) return -10;
+  if (o->n_want != 0) return GEP_ERR_UNSUPPORTED;
   for (int i = 0; i < count; ++i) {
     gep_options oi = *o;
     if (precision) oi.precision = precision[i];
@@ -810,10 +918,12 @@ int gep_solve_host(gep_handle_t h, int M, const double* A, int lda, const double
   if (ldb < (M > 1 ? M : 1)) return -6;
   if (M > 0 && !w) return -7;
   if (!o) return -10;
+  if (o->n_want < 0 || o->n_want > M) return -10;
   if (o->want_vectors && M > 0 && !Y) return -8;
   if (o->want_vectors && ldy < (M > 1 ? M : 1)) return -9;
   GEP_CHECK(check_opts(o));
   if (M == 0) return GEP_OK;
+  const int n = o->n_want > 0 ? o->n_want : M;
   size_t need = 0;
   GEP_CHECK(gep_workspace_size_host(h, M, o, &need));
   if (h->ws == nullptr || h->ws_bytes < need) return GEP_ERR_ALLOC;
@@ -839,10 +949,10 @@ int gep_solve_host(gep_handle_t h, int M, const double* A, int lda, const double
   h->ws = saved_ws;
   h->ws_bytes = saved_b;
   if (rc != GEP_OK) return rc;
-  GEP_CUDA(cudaMemcpyAsync(w, dw, (size_t)M * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GEP_CUDA(cudaMemcpyAsync(w, dw, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (o->want_vectors)
     GEP_CUDA(cudaMemcpy2DAsync(Y, (size_t)ldy * sizeof(double), dY, (size_t)M * sizeof(double), (size_t)M * sizeof(double),
-                               M, cudaMemcpyDeviceToHost, s));
+                               n, cudaMemcpyDeviceToHost, s));
   GEP_CUDA(cudaStreamSynchronize(s));
   return GEP_OK;
 }

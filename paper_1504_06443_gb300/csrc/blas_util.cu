@@ -76,6 +76,27 @@ __global__ void k_sym_part(int M, const double* __restrict__ W, int ldw, double*
   }
 }
 
+// Number of d_i <= 0 (or not finite): recorded as the numerical status when nonzero.
+__global__ void k_count_nonpositive(int M, const double* __restrict__ d, int* st) {
+  __shared__ int cnt;
+  if (status_bad(st)) return;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int c = 0;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) c += (d[i] > 0.0 && isfinite(d[i])) ? 0 : 1;
+  if (c) atomicAdd(&cnt, c);
+  __syncthreads();
+  if (threadIdx.x == 0 && cnt > 0) atomicCAS(st, 0, cnt);
+}
+
+// X(:, j) *= 1 / sqrt(d_j)
+__global__ void k_scale_cols_rsqrt(int m, int n, const double* __restrict__ d, double* X, int ldx, const int* st) {
+  if (status_bad(st)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int j = blockIdx.y; j < n; j += gridDim.y)
+    if (i < m) X[GEP_IX(i, j, ldx)] /= sqrt(d[j]);
+}
+
 __global__ void k_zero_upper(int M, double* A, int lda) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   for (int j = blockIdx.y; j < M; j += gridDim.y)
@@ -152,6 +173,14 @@ int symmetric_part(gep_handle_t h, int M, const double* W, int ldw, double* X, i
   if (M <= 0) return GEP_OK;
   dim3 g((M + 31) / 32, (M + 31) / 32);
   k_sym_part<<<g, dim3(32, 8), 0, h->stream>>>(M, W, ldw, X, ldx);
+  return check_launch(h);
+}
+
+int scale_cols_rsqrt_checked(gep_handle_t h, int m, int n, const double* d, double* X, int ldx) {
+  if (m <= 0 || n <= 0) return GEP_OK;
+  k_count_nonpositive<<<1, 256, 0, h->stream>>>(n, d, h->d_status);
+  GEP_CHECK(check_launch(h));
+  k_scale_cols_rsqrt<<<grid2(m, n), 256, 0, h->stream>>>(m, n, d, X, ldx, h->d_status);
   return check_launch(h);
 }
 

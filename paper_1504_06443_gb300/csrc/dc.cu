@@ -595,11 +595,12 @@ __device__ int sturm(int M, const double* __restrict__ d, const double* __restri
   return cnt;
 }
 
-__global__ void k_bisect(int M, const double* __restrict__ d, const double* __restrict__ e,
+// w[k], k < n: the (k+1)-th smallest eigenvalue of T (order M) by bisection on Sturm counts.
+__global__ void k_bisect(int n, int M, const double* __restrict__ d, const double* __restrict__ e,
                          const double* __restrict__ gb, double* __restrict__ w, const int* st) {
   if (status_bad(st)) return;
   int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= M) return;
+  if (k >= n) return;
   double a = gb[0], b = gb[1];
   for (int it = 0; it < 200; ++it) {
     double mid = 0.5 * (a + b);
@@ -611,12 +612,14 @@ __global__ void k_bisect(int M, const double* __restrict__ d, const double* __re
 
 }  // namespace
 
-int tridiag_eig_bisect(gep_handle_t h, int M, const double* d, const double* e, double* w) {
+int tridiag_eig_bisect(gep_handle_t h, int M, const double* d, const double* e, double* w, int n) {
   if (M <= 0) return GEP_OK;
+  if (n < 0 || n > M) n = M;  // the n lowest eigenvalues w[0..n)
+  if (n == 0) return GEP_OK;
   double* gb = (double*)(h->d_status + 8);  // two doubles of the handle's status block
   k_gersh<<<1, 1024, 0, h->stream>>>(M, d, e, gb);
   GEP_CHECK(check_launch(h));
-  k_bisect<<<(M + 127) / 128, 128, 0, h->stream>>>(M, d, e, gb, w, h->d_status);
+  k_bisect<<<(n + 127) / 128, 128, 0, h->stream>>>(n, M, d, e, gb, w, h->d_status);
   return check_launch(h);
 }
 

@@ -381,9 +381,11 @@ __device__ __forceinline__ double fixed_to_double(long long hi, long long lo, in
   return __longlong_as_double((long long)bits);
 }
 
+constexpr int GROUP_M = 8;  // row tiles per group of the tile order (L2 reuse of the A planes)
+
 struct OzArgs {
   int m, n, kpad, S, lmax, lower;
-  int gx, ntiles;  // tile grid: tile t covers rows 128 (t % gx) .., columns 64 (t / gx) ..
+  int gx, gy, ntiles;  // tile grid gx x gy (128-row x 64-column tiles), in grouped order
   const int* ea;
   const int* eb;
   double alpha, beta;
@@ -404,10 +406,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ int skip;
   // persistent: CTA b takes tiles b, b + gridDim.x, ...; tiles strictly above the
-  // diagonal of a lower-triangle product are skipped by every role alike
+  // diagonal of a lower-triangle product are skipped by every role alike.  Tiles are
+  // numbered in groups of GROUP_M row tiles, row fastest inside a group: the tiles that run
+  // at the same time cover a near-square block of C (8 rows x ~19 columns on 152 SMs), so
+  // their A and B planes are read from DRAM about once and then hit in L2.
   auto tile_rc = [&](int t, int& tm, int& tn) {
-    tm = (t % p.gx) * TM;
-    tn = (t / p.gx) * TN;
+    const int per_group = GROUP_M * p.gy;
+    const int first = (t / per_group) * GROUP_M;
+    const int gm = min(p.gx - first, GROUP_M);
+    const int local = t - (first / GROUP_M) * per_group;
+    tm = (first + local % gm) * TM;
+    tn = (local / gm) * TN;
     return !(p.lower && tm + TM - 1 < tn);
   };
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -701,6 +710,7 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
     a.ea = ea; a.eb = eb; a.alpha = alpha; a.beta = (kb == 0) ? beta : 1.0; a.C = C; a.ldc = ldc; a.st = h->d_status;
     const int gx = (m + TM - 1) / TM, gy = (n + TN - 1) / TN;
     a.gx = gx;
+    a.gy = gy;
     a.ntiles = gx * gy;
     dim3 grid(a.ntiles < h->sm_count ? a.ntiles : h->sm_count);  // persistent CTAs
     int slot = -1;

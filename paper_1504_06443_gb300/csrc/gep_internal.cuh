@@ -129,6 +129,8 @@ int symmetrize_lower(gep_handle_t h, int M, double* A, int lda);  // upper := lo
 int transpose(gep_handle_t h, int m, int n, const double* src, int lds, double* dst, int ldd);
 int zero_upper(gep_handle_t h, int M, double* A, int lda);          // strict upper := 0
 int symmetric_part(gep_handle_t h, int M, const double* W, int ldw, double* X, int ldx);  // X = (W + W^T) / 2
+// X(:, j) *= d_j^-1/2 (m x n); first records the number of d_j <= 0 as numerical status k > 0
+int scale_cols_rsqrt_checked(gep_handle_t h, int m, int n, const double* d, double* X, int ldx);
 int scan_nonfinite(gep_handle_t h, int M, const double* A, int lda);  // lower triangle
 
 // ---- triangular building blocks (tri.cu) ----
@@ -172,7 +174,7 @@ size_t backtransform_ws_elems(int M, int ncol);
 int tridiag_eig_dc(gep_handle_t h, int M, const double* d, const double* e, double* w, double* Z,
                    int ldz, double* ws, size_t ws_elems, int engine);
 size_t dc_ws_bytes(int M);
-int tridiag_eig_bisect(gep_handle_t h, int M, const double* d, const double* e, double* w);
+int tridiag_eig_bisect(gep_handle_t h, int M, const double* d, const double* e, double* w, int n = -1);
 int sign_convention(gep_handle_t h, int M, int ncol, double* Y, int ldy);
 size_t refine_ws_elems(int M);
 int refine_eigenpairs(gep_handle_t h, int M, const double* Af, const double* Bf, double* X, int ldx, double* w,

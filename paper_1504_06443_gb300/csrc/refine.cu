@@ -49,7 +49,8 @@ __global__ void __launch_bounds__(1024) k_rayleigh(int M, const double* __restri
   }
 }
 
-constexpr int KMAX = 32;              // largest cluster solved exactly, also the pair window
+constexpr int KMAX = 32;              // largest cluster solved by one thread, also the pair window
+constexpr int KBIG = 256;             // largest cluster solved exactly (one CTA above KMAX)
 constexpr double THETA = 64;          // |gap| < THETA res_ij: first-order step not small
 constexpr double OMEGA_GLOBAL = 16;   // |gap| < 16 max res: below the current error level
 constexpr double OMEGA_FLOOR = 1e-6;  // |gap| < 1e-6 max|lambda|: unresolvable at FP64
@@ -92,10 +93,10 @@ __global__ void k_pair_far(int M, const double* __restrict__ S, const double* __
 
 // Clusters = unions of the overlapping index ranges [i, far[i]] (serial scan, one
 // thread): cstart/csize/coff (scratch offset) per cluster, ncl[0] = number of clusters,
-// cid[i] = the cluster of index i when that cluster is solved exactly (k <= KMAX),
-// -2 - c when i lies in cluster c of more than KMAX members (chained near-degenerate
+// cid[i] = the cluster of index i when that cluster is solved exactly (k <= KBIG),
+// -2 - c when i lies in cluster c of more than KBIG members (chained near-degenerate
 // eigenvalues; its inner pairs only get their B-orthogonality restored), else -1.
-// Scratch use is sum 3 k^2 <= 3 M min(M, KMAX).
+// Scratch use is sum 3 k^2 <= 3 M min(M, KBIG).
 __global__ void k_clusters(int M, const int* __restrict__ far, int* cstart, int* csize, long long* coff, int* cid,
                            int* ncl, const int* st) {
   if (status_bad(st)) return;
@@ -112,9 +113,9 @@ __global__ void k_clusters(int M, const int* __restrict__ far, int* cstart, int*
       cstart[nc] = i;
       csize[nc] = k;
       coff[nc] = used;
-      if (k <= KMAX) used += 3LL * k * k;
+      if (k <= KBIG) used += 3LL * k * k;
     }
-    for (int q = i; q <= end; ++q) cid[q] = (k > 1 && k <= KMAX) ? nc : (k > KMAX ? -2 - nc : -1);
+    for (int q = i; q <= end; ++q) cid[q] = (k > 1 && k <= KBIG) ? nc : (k > KBIG ? -2 - nc : -1);
     if (k > 1) ++nc;
     i = end + 1;
   }
@@ -299,11 +300,230 @@ __global__ void k_cluster_solve(int M, const double* __restrict__ S, const doubl
   }
 }
 
+// One CTA per cluster of KMAX < k <= KBIG members (a chain of near-degenerate eigenvalues):
+// the exact solve of k_cluster_solve with its steps spread over the CTA.  The triangular
+// solves take one column (row) per thread; cyclic Jacobi runs in round-robin order, whose
+// k/2 rotations of a round touch disjoint index pairs and are applied together.
+__global__ void __launch_bounds__(256) k_cluster_solve_big(int M, const double* __restrict__ S,
+                                                           const double* __restrict__ R,
+                                                           const int* __restrict__ cstart,
+                                                           const int* __restrict__ csize,
+                                                           const long long* __restrict__ coff, const int* ncl,
+                                                           double* __restrict__ lam, double* __restrict__ E,
+                                                           double* __restrict__ scratch, const int* st) {
+  __shared__ double csv[KBIG / 2], snv[KBIG / 2], red[8];
+  __shared__ int pa[KBIG / 2], pb[KBIG / 2], pos[KBIG];
+  __shared__ int done;
+  if (status_bad(st)) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int c = blockIdx.x; c < ncl[0]; c += gridDim.x) {
+    const int s0 = cstart[c], k = csize[c];
+    if (k <= KMAX || k > KBIG) continue;
+    double* L = scratch + coff[c];
+    double* Cm = L + (size_t)k * k;
+    double* V = Cm + (size_t)k * k;
+    for (int idx = tid; idx < k * k; idx += nt) {
+      int p = idx % k, q = idx / k;
+      int a = max(s0 + p, s0 + q), b = min(s0 + p, s0 + q);
+      L[idx] = R[GEP_IX(a, b, M)];
+      Cm[idx] = S[GEP_IX(a, b, M)];
+      V[idx] = (p == q) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    // Cholesky R_CC = L L^T (right-looking, lower triangle)
+    for (int j = 0; j < k; ++j) {
+      if (tid == 0) L[j + j * k] = sqrt(fmax(L[j + j * k], 1e-300));
+      __syncthreads();
+      const double d = L[j + j * k];
+      for (int i = j + 1 + tid; i < k; i += nt) L[i + j * k] /= d;
+      __syncthreads();
+      const int w = k - j - 1;
+      for (int t = tid; t < w * w; t += nt) {
+        int i = j + 1 + t % w, q = j + 1 + t / w;
+        if (i >= q) L[i + q * k] -= L[i + j * k] * L[q + j * k];
+      }
+      __syncthreads();
+    }
+    // Cm <- L^-1 Cm (each column a forward substitution), then Cm <- Cm L^-T (each row)
+    for (int q = tid; q < k; q += nt)
+      for (int i = 0; i < k; ++i) {
+        double t = Cm[i + q * k];
+        for (int p = 0; p < i; ++p) t -= L[i + p * k] * Cm[p + q * k];
+        Cm[i + q * k] = t / L[i + i * k];
+      }
+    __syncthreads();
+    for (int i = tid; i < k; i += nt)
+      for (int q = 0; q < k; ++q) {
+        double t = Cm[i + q * k];
+        for (int p = 0; p < q; ++p) t -= Cm[i + p * k] * L[q + p * k];
+        Cm[i + q * k] = t / L[q + q * k];
+      }
+    __syncthreads();
+    // parallel cyclic Jacobi: n = k rounded up to even (index k, if present, is a dummy)
+    const int n = (k + 1) & ~1, half = n / 2;
+    for (int i = tid; i < n; i += nt) pos[i] = i;
+    if (tid == 0) done = 0;
+    __syncthreads();
+    for (int sweep = 0; sweep < 30 && !done; ++sweep) {
+      double off = 0.0, tot = 0.0;
+      for (int idx = tid; idx < k * k; idx += nt) {
+        double x = Cm[idx];
+        tot += x * x;
+        if (idx % k != idx / k) off += x * x;
+      }
+      for (int o = 16; o; o >>= 1) {
+        off += __shfl_xor_sync(0xffffffffu, off, o);
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      }
+      if ((tid & 31) == 0) { red[tid >> 5] = off; }
+      __syncthreads();
+      if (tid == 0) {
+        double so = 0.0;
+        for (int w = 0; w < nt / 32; ++w) so += red[w];
+        red[0] = so;
+      }
+      __syncthreads();
+      const double offs = red[0];
+      __syncthreads();
+      if ((tid & 31) == 0) red[tid >> 5] = tot;
+      __syncthreads();
+      if (tid == 0) {
+        double st2 = 0.0;
+        for (int w = 0; w < nt / 32; ++w) st2 += red[w];
+        done = offs <= 1e-28 * st2;  // off-diagonal entries ~1e-14 of the matrix: FP64 level
+      }
+      __syncthreads();
+      if (done) break;
+      for (int round = 0; round < n - 1; ++round) {
+        for (int t = tid; t < half; t += nt) {
+          int a = pos[t], b = pos[n - 1 - t];
+          int p = min(a, b), q = max(a, b);
+          double cs = 1.0, sn = 0.0;
+          if (q < k) {
+            double apq = 0.5 * (Cm[p + q * k] + Cm[q + p * k]);
+            if (apq != 0.0) {
+              double th = (Cm[q + q * k] - Cm[p + p * k]) / (2.0 * apq);
+              double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+              cs = 1.0 / sqrt(tt * tt + 1.0);
+              sn = tt * cs;
+            }
+          }
+          pa[t] = p;
+          pb[t] = q;
+          csv[t] = cs;
+          snv[t] = sn;
+        }
+        __syncthreads();
+        // columns of Cm and V
+        for (int idx = tid; idx < half * k; idx += nt) {
+          int t = idx / k, r = idx % k;
+          if (pb[t] >= k || snv[t] == 0.0) continue;
+          int p = pa[t], q = pb[t];
+          double cs = csv[t], sn = snv[t];
+          double x = Cm[r + p * k], y = Cm[r + q * k];
+          Cm[r + p * k] = cs * x - sn * y;
+          Cm[r + q * k] = sn * x + cs * y;
+          x = V[r + p * k];
+          y = V[r + q * k];
+          V[r + p * k] = cs * x - sn * y;
+          V[r + q * k] = sn * x + cs * y;
+        }
+        __syncthreads();
+        // rows of Cm
+        for (int idx = tid; idx < half * k; idx += nt) {
+          int t = idx / k, r = idx % k;
+          if (pb[t] >= k || snv[t] == 0.0) continue;
+          int p = pa[t], q = pb[t];
+          double cs = csv[t], sn = snv[t];
+          double x = Cm[p + r * k], y = Cm[q + r * k];
+          Cm[p + r * k] = cs * x - sn * y;
+          Cm[q + r * k] = sn * x + cs * y;
+        }
+        __syncthreads();
+        if (tid == 0) {  // round-robin: position 0 stays, the others rotate by one
+          int last = pos[n - 1];
+          for (int i = n - 1; i > 1; --i) pos[i] = pos[i - 1];
+          pos[1] = last;
+        }
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+    // ascending order of the cluster's eigenvalues (selection sort; column swaps in parallel)
+    for (int a = 0; a < k; ++a) {
+      if (tid == 0) {
+        int m = a;
+        for (int b = a + 1; b < k; ++b)
+          if (Cm[b + b * k] < Cm[m + m * k]) m = b;
+        pos[0] = m;
+      }
+      __syncthreads();
+      const int m = pos[0];
+      if (m != a) {
+        for (int r = tid; r < k; r += nt) {
+          double x = V[r + a * k];
+          V[r + a * k] = V[r + m * k];
+          V[r + m * k] = x;
+        }
+        if (tid == 0) {
+          double t = Cm[a + a * k];
+          Cm[a + a * k] = Cm[m + m * k];
+          Cm[m + m * k] = t;
+        }
+      }
+      __syncthreads();
+    }
+    // W = L^-T V (each column a back substitution), E_CC = W - I
+    for (int q = tid; q < k; q += nt) {
+      for (int i = k - 1; i >= 0; --i) {
+        double t = V[i + q * k];
+        for (int p = i + 1; p < k; ++p) t -= L[p + i * k] * V[p + q * k];
+        V[i + q * k] = t / L[i + i * k];
+      }
+      for (int p = 0; p < k; ++p) E[GEP_IX(s0 + p, s0 + q, M)] = V[p + q * k] - (p == q ? 1.0 : 0.0);
+      lam[s0 + q] = Cm[q + q * k];
+    }
+    __syncthreads();
+  }
+}
+
+// E_{j,C} <- E_{j,C} W_C for the rows j outside every cluster C of KMAX < k <= KBIG members
+// (W_C left in the cluster's scratch by k_cluster_solve_big); CTA: 8 rows, staged in shared
+// memory, one loop over the clusters.
+__global__ void __launch_bounds__(256) k_cluster_rotate_big(int M, const int* __restrict__ cstart,
+                                                            const int* __restrict__ csize,
+                                                            const long long* __restrict__ coff, const int* ncl,
+                                                            const double* __restrict__ scratch, double* __restrict__ E,
+                                                            const int* st) {
+  __shared__ double rows[8][KBIG];
+  if (status_bad(st)) return;
+  const int j0 = blockIdx.x * 8, tid = threadIdx.x;
+  const int nc = ncl[0];
+  for (int c = 0; c < nc; ++c) {
+    const int s0 = cstart[c], k = csize[c];
+    if (k <= KMAX || k > KBIG) continue;
+    const double* W = scratch + coff[c] + 2 * (size_t)k * k;
+    for (int idx = tid; idx < 8 * k; idx += blockDim.x) {
+      int r = idx / k, p = idx % k, j = j0 + r;
+      rows[r][p] = (j < M) ? E[GEP_IX(j, s0 + p, M)] : 0.0;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 8 * k; idx += blockDim.x) {
+      int r = idx / k, q = idx % k, j = j0 + r;
+      if (j >= M || (j >= s0 && j < s0 + k)) continue;
+      double t = 0.0;
+      for (int p = 0; p < k; ++p) t = fma(rows[r][p], W[p + (size_t)q * k], t);
+      E[GEP_IX(j, s0 + q, M)] = t;
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 size_t refine_ws_elems(int M) {
   auto r = [](size_t n) { return (n + 31) & ~(size_t)31; };
-  size_t kmax = M < KMAX ? (size_t)M : (size_t)KMAX;
+  size_t kmax = M < KBIG ? (size_t)M : (size_t)KBIG;
   // T1, S, R, E; conv; far, cstart, csize, cid (ints) and coff (int64) per index; cluster scratch
   return 4 * r((size_t)M * M) + 32 + 2 * r((size_t)M) + r((size_t)M) + r(3 * (size_t)M * kmax) + 32;
 }
@@ -330,7 +550,7 @@ int refine_eigenpairs(gep_handle_t h, int M, const double* Af, const double* Bf,
   int* cid = csize + M;  // four int arrays fit in 2 r(M) doubles
   long long* coff = reinterpret_cast<long long*>(conv + 32 + 2 * r((size_t)M));
   double* scratch = conv + 32 + 3 * r((size_t)M);
-  int* ncl = reinterpret_cast<int*>(scratch + r(3 * (size_t)M * (M < KMAX ? M : KMAX)));
+  int* ncl = reinterpret_cast<int*>(scratch + r(3 * (size_t)M * (M < KBIG ? M : KBIG)));
   bool adaptive = iters == 0;
   if (adaptive) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -360,6 +580,14 @@ int refine_eigenpairs(gep_handle_t h, int M, const double* Af, const double* Bf,
     GEP_CHECK(check_launch(h));
     k_cluster_rotate<<<(M + 127) / 128, 128, 0, h->stream>>>(M, cstart, csize, coff, ncl, scratch, E, h->d_status);
     GEP_CHECK(check_launch(h));
+    if (M > KMAX) {  // clusters of KMAX < k <= KBIG members (chains of near-degenerate eigenvalues)
+      k_cluster_solve_big<<<h->sm_count, 256, 0, h->stream>>>(M, S, R, cstart, csize, coff, ncl, w, E, scratch,
+                                                              h->d_status);
+      GEP_CHECK(check_launch(h));
+      k_cluster_rotate_big<<<(M + 7) / 8, 256, 0, h->stream>>>(M, cstart, csize, coff, ncl, scratch, E,
+                                                               h->d_status);
+      GEP_CHECK(check_launch(h));
+    }
     GEP_CHECK(copy_matrix(h, M, M, X, ldx, T1, M));
     GEP_CHECK(dgemm(h, 'N', 'N', 'F', M, M, M, 1.0, T1, M, E, M, 1.0, X, ldx, engine));   // X <- X + X E
     h->refine_steps = it + 1;

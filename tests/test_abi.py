@@ -85,3 +85,21 @@ def test_host_checks_without_gpu(libpath):
     assert lib.sep_q2_elems(100, 0) == 0 and lib.sep_q2_elems(1, 8) == 0
     # (Q + 1)(Q + 2)/2 diamonds of 3b^2 + b doubles, Q = (M - 2) / b
     assert lib.sep_q2_elems(100, 8) == (12 + 1) * (12 + 2) // 2 * (3 * 64 + 8)
+
+
+def test_options_struct_layout_matches_binding(tmp_path):
+    """The binding's ctypes mirror of gep_options has the C struct's size and field offsets."""
+    import paper_1504_06443_gb300 as g
+    src = tmp_path / "lay.c"
+    fields = [f for f, _ in g.GepOptions._fields_]
+    body = "".join(f'printf("%zu ", offsetof(gep_options, {f}));' for f in fields)
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gep.h"\n'
+                   f'int main(void){{{body} printf("%zu", sizeof(gep_options)); return 0;}}\n')
+    exe = tmp_path / "lay"
+    r = subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    import ctypes
+    assert out[-1] == ctypes.sizeof(g.GepOptions)
+    assert out[:-1] == [getattr(g.GepOptions, f).offset for f in fields]
