@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--batch-count", type=int, default=512)
     p.add_argument("--adjoint", action="store_true",
                    help="forward+adjoint of sum(lambda_occ) + <W, P> at M=4096 with central differences")
-    p.add_argument("--fd-dirs", type=int, default=8)
+    p.add_argument("--fd-dirs", type=int, default=64)
     return p.parse_args()
 
 
@@ -66,7 +66,27 @@ def _median_clock(clk):
     return clk.stop()
 
 
+def spectral_norm_lower_bound(A, iters=200, seed=0):
+    """||A||_2 from below by power iteration (plain torch FP64): a conservative stand-in for
+    the 2-norm in the |dlambda| <= 1e-11 ||A||_2 tolerance where a full eigensolve is too slow."""
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    v = torch.randn(A.shape[0], generator=g, dtype=torch.float64).to(A.device)
+    v /= v.norm()
+    lam = 0.0
+    for _ in range(iters):
+        u = A @ v
+        lam = float(u.norm())
+        v = u / lam
+    return lam
+
+
 def run_compare_mixed(a):
+    """Config 3: the mixed-precision form (FP32-grade split-BF16 products, then FP64 refinement)
+    against the plain FP64 form (every product on the FP64 units) and the FP64-accurate
+    split-BF16 form, on the same pencil: wall time, stage times, and the error of the
+    FP32-grade first pass alone and of the refined result, in |dlambda| / ||A||_2 against
+    the FP64 forms, sampled residual and B-orthogonality."""
     import torch
     import gep_inputs as gi
     from paper_1504_06443_gb300 import build as gbuild
@@ -76,35 +96,41 @@ def run_compare_mixed(a):
     tb = gi.tight_binding(M, a.seed)
     A = torch.as_tensor(tb["A"]).cuda()
     B = torch.as_tensor(tb["B"]).cuda()
-    out = {"metric": "mixed+refined vs FP64-accurate GEP solve time", "M": M, "unit": "s",
-           "higher_is_better": False, "data": "synthetic",
-           "config": {"workload": f"tight-binding GEP M={M}", "sep": a.sep}}
-    res = {}
-    for prec in ("fp64_emulated", "mixed_refined"):
+    nA = spectral_norm_lower_bound(A)
+    routes = [("fp64", "fp64", 0), ("fp64_emulated", "fp64_emulated", 0), ("mixed_refined", "mixed_refined", 0),
+              ("mixed_first_pass", "mixed_refined", -1)]
+    res, ws = {}, {}
+    for name, prec, iters in routes:
         h = gep.Handle()
-        for _ in range(max(1, a.warmup)):
-            w, Y, info = gep.solve(A, B, precision=prec, timers=True, handle=h, sep=a.sep)
+        steps = 1 if prec == "fp64" else a.steps
+        for _ in range(max(1, a.warmup) if prec != "fp64" else 1):
+            w, Y, info = gep.solve(A, B, precision=prec, timers=True, handle=h, sep=a.sep, refine_iters=iters)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(a.steps):
-            w, Y, info = gep.solve(A, B, precision=prec, timers=True, handle=h, sep=a.sep)
+        for _ in range(steps):
+            w, Y, info = gep.solve(A, B, precision=prec, timers=True, handle=h, sep=a.sep, refine_iters=iters)
         e1.record()
         torch.cuda.synchronize()
-        res[prec] = {"s": e0.elapsed_time(e1) / a.steps / 1e3, "info": info,
+        res[name] = {"s": e0.elapsed_time(e1) / steps / 1e3, "steps": steps, "info": info,
                      "stage_ms": [round(x, 1) for x in h.stage_times()],
                      "check": sampled_check(A, B, w, Y, 64, a.seed),
                      "refine_steps": h.refine_steps() if prec == "mixed_refined" else 0}
-        res[prec]["w"] = w.clone()
+        ws[name] = w.clone()
+        del Y
         h.close()
-    nA = float(torch.linalg.eigvalsh(A).abs().max().item()) if M <= 8192 else float(A.abs().sum(1).max().item())
-    dw = float((res["mixed_refined"]["w"] - res["fp64_emulated"]["w"]).abs().max().item())
-    for r in res.values():
-        r.pop("w")
-    out.update({"fp64": res["fp64_emulated"], "mixed_refined": res["mixed_refined"],
-                "max_abs_dlambda_over_normA": dw / nA,
-                "normA_kind": "2-norm" if M <= 8192 else "row-sum bound (>= 2-norm)",
-                "speedup_mixed_vs_fp64": res["fp64_emulated"]["s"] / res["mixed_refined"]["s"]})
+        torch.cuda.empty_cache()
+    for name in res:
+        res[name]["max_abs_dlambda_vs_fp64_over_normA"] = float((ws[name] - ws["fp64"]).abs().max()) / nA
+        res[name]["max_abs_dlambda_vs_fp64_emulated_over_normA"] = float((ws[name] - ws["fp64_emulated"]).abs().max()) / nA
+    out = {"metric": "mixed+refined vs FP64 GEP solve time at 1e-11 ||A||_2", "M": M, "unit": "s",
+           "higher_is_better": False, "data": "synthetic", "dtype": "f64",
+           "config": {"workload": f"tight-binding GEP M={M} ({M // 4} atoms), all eigenpairs", "sep": a.sep},
+           "normA_2_lower_bound": nA, "normA_kind": "power iteration (200 steps), a lower bound of ||A||_2",
+           "routes": res,
+           "speedup_mixed_vs_fp64": res["fp64"]["s"] / res["mixed_refined"]["s"],
+           "speedup_mixed_vs_fp64_emulated": res["fp64_emulated"]["s"] / res["mixed_refined"]["s"],
+           "mixed_meets_1e-11": res["mixed_refined"]["max_abs_dlambda_vs_fp64_over_normA"] <= 1e-11}
     print(json.dumps(out), flush=True)
 
 

@@ -73,7 +73,8 @@ typedef struct gep_options {
   int want_vectors; /* 1: eigenpairs (T_full); 0: eigenvalues only (T_evo)        */
   int overwrite;    /* 1: A and B may be destroyed by gep_solve (saves two copies) */
   int timers;       /* 1: record per-stage CUDA-event times (gep_get_stage_times) */
-  int refine_iters; /* GEP_PREC_MIXED_REFINED: FP64 refinement steps; 0 = until converged */
+  int refine_iters; /* GEP_PREC_MIXED_REFINED: FP64 refinement steps; 0 = until converged;
+                       -1 = none (the FP32-grade first pass alone, for error studies) */
   int n_want;       /* 0: all M eigenpairs; 1..M: only the n_want lowest (section 2: the occupied
                        states), w[0..n_want) and Y M x n_want.  Eigenvalues only: bisection for
                        those indices; with vectors: divide and conquer gives every eigenvector of

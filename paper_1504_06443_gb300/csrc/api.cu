@@ -15,7 +15,7 @@ constexpr int NB = 128;  // diagonal block order of the triangular kernels (tri.
 bool handle_ok(gep_handle_t h) { return h != nullptr && h->magic == 0x6e70; }
 
 struct SolveLayout {
-  size_t Cw, Lw, invD, vec, uni, eng, af, q2, xw, zt, end;  // byte offsets
+  size_t Cw, Lw, invD, vec, uni, eng, af, q2, xw, zt, q2u, end;  // byte offsets
   size_t uni_bytes, eng_bytes;
 };
 
@@ -29,6 +29,10 @@ bool sep_vectors(const gep_options* o) { return o->want_vectors || eigenexa(o); 
 // only the lowest n_want eigenpairs, with vectors: D&C writes all eigenvectors of T to a
 // workspace matrix first
 bool partial_vectors(int M, const gep_options* o) { return o->want_vectors && o->n_want > 0 && o->n_want < M; }
+// the tensor-core engines apply Q2 as dense tiles, all built ahead on the second stream
+bool q2_tiles_ahead(const gep_options* o) {
+  return two_stage(o) && sep_vectors(o) && o->precision != GEP_PREC_FP64;
+}
 
 size_t r256(size_t x) { return align256(x); }
 
@@ -85,6 +89,8 @@ SolveLayout layout(int M, const gep_options* o) {
   off += eigenexa(o) ? r256(mm) : 0;
   L.zt = off;  // all eigenvectors of T when only the lowest n_want are back-transformed
   off += partial_vectors(M, o) ? r256(mm) : 0;
+  L.q2u = off;  // every dense Q2 tile, built on the second stream during divide and conquer
+  off += q2_tiles_ahead(o) ? r256(q2_all_tiles_elems(M, band_of(o)) * sizeof(double)) : 0;
   L.end = off;
   return L;
 }
@@ -99,7 +105,7 @@ int check_opts(const gep_options* o) {
       o->precision != GEP_PREC_MIXED_REFINED)
     return GEP_ERR_UNSUPPORTED;
   if (o->precision == GEP_PREC_MIXED_REFINED && !o->want_vectors) return GEP_ERR_UNSUPPORTED;
-  if (o->refine_iters < 0) return -10;
+  if (o->refine_iters < -1) return -10;
   if (o->n_want < 0) return -10;
   if (o->n_want > 0 && o->precision == GEP_PREC_MIXED_REFINED) return GEP_ERR_UNSUPPORTED;
   return GEP_OK;
@@ -123,7 +129,7 @@ void mark(gep_handle_t h, const gep_options* o, int i) {
 // (after TRD/BAND) and 4 (after D&C) and the S1b/S1c split of the caller's timers.
 int sep_solve(gep_handle_t h, int M, double* C, int ldc, const gep_options* o, double* dvec, double* evec,
               double* tvec, double* q2, char* uni, size_t uni_bytes, int eng, double* w, double* Z, int ldz,
-              bool timed, int n = 0, double* Zt = nullptr, double* wt = nullptr) {
+              bool timed, int n = 0, double* Zt = nullptr, double* wt = nullptr, double* q2u = nullptr) {
   if (n <= 0 || n > M) n = M;
   const int bw = band_of(o);
   if (two_stage(o)) {
@@ -140,6 +146,15 @@ int sep_solve(gep_handle_t h, int M, double* C, int ldc, const gep_options* o, d
     if (timed) mark(h, o, 4);
     return GEP_OK;
   }
+  // the Q2 tiles depend only on the bulge-chasing reflectors: build them on the second
+  // stream while divide and conquer runs here
+  const bool ahead = q2u != nullptr && two_stage(o) && eng != GEP_PREC_FP64;
+  if (ahead) {
+    GEP_CUDA(cudaEventRecord(h->ev_fork, h->stream));
+    GEP_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    GEP_CHECK(build_q2_tiles(h, h->side, M, band_of(o), q2, q2u));
+    GEP_CUDA(cudaEventRecord(h->ev_join, h->side));
+  }
   if (n < M) {
     if (!Zt || !wt) return GEP_ERR_ALLOC;
     GEP_CHECK(tridiag_eig_dc(h, M, dvec, evec, wt, Zt, M, (double*)uni, uni_bytes, eng));  // D&C
@@ -149,8 +164,10 @@ int sep_solve(gep_handle_t h, int M, double* C, int ldc, const gep_options* o, d
     GEP_CHECK(tridiag_eig_dc(h, M, dvec, evec, w, Z, ldz, (double*)uni, uni_bytes, eng));  // D&C
   }
   if (timed) mark(h, o, 4);
+  if (ahead) GEP_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
   if (two_stage(o)) {
-    GEP_CHECK(apply_q2(h, M, bw, q2, Z, ldz, n, eng, (double*)uni, uni_bytes / sizeof(double)));
+    GEP_CHECK(apply_q2(h, M, bw, q2, Z, ldz, n, eng, (double*)uni, uni_bytes / sizeof(double),
+                       ahead ? q2u : nullptr));
     return backtransform_q(h, M, n, C, ldc, tvec, Z, ldz, (double*)uni, uni_bytes / sizeof(double), eng, bw);
   }
   return backtransform_q(h, M, n, C, ldc, tvec, Z, ldz, (double*)uni, uni_bytes / sizeof(double), eng);
@@ -187,6 +204,12 @@ int gep_create(gep_handle_t* out, void* stream) {
   }
   for (int i = 0; i < 8; ++i) cudaEventCreate(&h->ev[i]);
   cudaEventCreate(&h->ev_band);
+  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    gep_destroy(h);
+    return GEP_ERR_CUDA;
+  }
   *out = h;
   return GEP_OK;
 }
@@ -203,6 +226,9 @@ int gep_destroy(gep_handle_t h) {
   cudaFree(h->d_batch_info);
   for (int i = 0; i < 8; ++i) cudaEventDestroy(h->ev[i]);
   cudaEventDestroy(h->ev_band);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
   cudaFree(h->d_status);
   cudaFree(h->d_splitk);
   h->magic = 0;
@@ -670,13 +696,15 @@ int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, dou
   double* wB = tvec + (M + 1);  // eigenvalues D of B (Cholesky-free reducer)
   double* wT = wB + (M + 1);     // all eigenvalues of T when only the lowest n are wanted
   double* Zt = partial_vectors(M, o) ? (double*)(base + Ly.zt) : nullptr;
+  double* q2u = q2_tiles_ahead(o) ? (double*)(base + Ly.q2u) : nullptr;
   h->band_recorded = two_stage(o) && o->timers;
   double* q2 = (two_stage(o) && sep_vectors(o)) ? (double*)(base + Ly.q2) : nullptr;
   mark(h, o, 0);
   if (eigenexa(o)) {
     // Eq. 7: B W = W D by the SEP solver (B's copy becomes its reflectors), X = W D^-1/2
     double* Xw = (double*)(base + Ly.xw);
-    GEP_CHECK(sep_solve(h, M, Lw, ldlw, o, dvec, evec, tvec, q2, uni, Ly.uni_bytes, eng, wB, Xw, M, false));
+    GEP_CHECK(sep_solve(h, M, Lw, ldlw, o, dvec, evec, tvec, q2, uni, Ly.uni_bytes, eng, wB, Xw, M, false, 0, nullptr,
+                        nullptr, q2u));
     GEP_CHECK(scale_cols_rsqrt_checked(h, M, M, wB, Xw, M));  // status k: k eigenvalues of B <= 0
     mark(h, o, 1);
     // Eq. 8: A' = X^T (A X), lower triangle (all the SEP solver reads)
@@ -687,7 +715,7 @@ int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, dou
     // A' Z = Z Lambda (Z into B's buffer, no longer needed), then Eq. 9: Y = X Z
     double* Z = o->want_vectors ? Lw : nullptr;
     GEP_CHECK(sep_solve(h, M, Cw, ldcw, o, dvec, evec, tvec, q2, uni, Ly.uni_bytes, eng, w, Z, ldlw, true, n, Zt,
-                        wT));
+                        wT, q2u));
     if (!o->want_vectors) {
       mark(h, o, 5);
       mark(h, o, 6);
@@ -713,7 +741,7 @@ int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, dou
     }
     mark(h, o, 2);
     GEP_CHECK(sep_solve(h, M, Cw, ldcw, o, dvec, evec, tvec, q2, uni, Ly.uni_bytes, eng, w,
-                        o->want_vectors ? Y : nullptr, ldy, true, n, Zt, wT));
+                        o->want_vectors ? Y : nullptr, ldy, true, n, Zt, wT, q2u));
     if (!o->want_vectors) {
       mark(h, o, 5);
       mark(h, o, 6);
@@ -731,7 +759,8 @@ int gep_solve(gep_handle_t h, int M, double* A, int lda, double* B, int ldb, dou
     }
     mark(h, o, 6);
   }
-  if (mixed) {
+  h->refine_steps = 0;
+  if (mixed && o->refine_iters >= 0) {
     GEP_CHECK(refine_eigenpairs(h, M, Af, Bf, Y, ldy, w, (double*)uni, o->refine_iters, GEP_PREC_FP64_EMULATED));
   }
   mark(h, o, 7);

@@ -937,11 +937,57 @@ size_t q2_tile_ws_elems(int M, int b) {
   return rr(nK * W * W) + rr(W * (size_t)M);
 }
 
+namespace {
+
+// Tiles of every tile row J, one after the other (tile (J, K) at all_tiles_offset(Q, J) + K).
+size_t all_tiles_offset(int Q, int J) {
+  size_t off = 0;
+  for (int j = 0; j < J; ++j) off += (size_t)((Q - j * TQ) / TQ + 1);
+  return off;
+}
+
+int set_tile_build_attr() {
+  static unsigned long long attr_devices = 0;
+  if (first_use_on_device(attr_devices))
+    GEP_CUDA(cudaFuncSetAttribute(k_q2_tile_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)q2_tile_smem_bytes(BMAX)));
+  return GEP_OK;
+}
+
+}  // namespace
+
+size_t q2_all_tiles_elems(int M, int b) {
+  if (M < 3 || b < 1) return 0;
+  const int Q = (M - 2) / b;
+  const size_t W = (size_t)2 * TQ * b;
+  return all_tiles_offset(Q, Q / TQ + 1) * W * W;
+}
+
+// Builds every dense tile U(J, K) - I of Q2 into U (q2_all_tiles_elems doubles) on `stream`,
+// for apply_q2 to use later; it only reads q2, so it may run on a second stream while the
+// tridiagonal eigensolver runs on the first.
+int build_q2_tiles(gep_handle_t h, cudaStream_t stream, int M, int b, const double* q2, double* U) {
+  if (b < 1 || b > BMAX) return GEP_ERR_UNSUPPORTED;
+  if (M < 3) return GEP_OK;
+  GEP_CHECK(set_tile_build_attr());
+  const int Q = (M - 2) / b;
+  const int W = 2 * TQ * b, nJ = Q / TQ + 1;
+  const size_t smem = q2_tile_smem_bytes(b);
+  for (int J = 0; J < nJ; ++J) {
+    const int nK = (Q - J * TQ) / TQ + 1;
+    double* UJ = U + all_tiles_offset(Q, J) * (size_t)W * W;
+    k_q2_tile_build<<<dim3(nK, (W + TB_COLS - 1) / TB_COLS), 256, smem, stream>>>(M, b, Q, J, q2, UJ, h->d_status);
+    GEP_CHECK(check_launch(h));
+  }
+  return GEP_OK;
+}
+
 // Z (M x ncol) <- Q2 Z.  engine FP64: diamonds applied directly on the FP64 cores.
 // Otherwise the diamonds are merged into dense W x W tiles U(J, R) and every tile is
 // applied as one product Z(rows) <- U Z(rows) on the engine (ws: q2_tile_ws_elems).
+// U_all != null: the tiles were built by build_q2_tiles (on the caller's stream order).
 int apply_q2(gep_handle_t h, int M, int b, const double* q2, double* Z, int ldz, int ncol, int engine, double* ws,
-             size_t ws_elems) {
+             size_t ws_elems, const double* U_all) {
   if (b < 1 || b > BMAX) return GEP_ERR_UNSUPPORTED;
   if (M < 3 || ncol <= 0) return GEP_OK;  // M = 2: the only reflector is the identity
   const int Q = (M - 2) / b;
@@ -949,18 +995,20 @@ int apply_q2(gep_handle_t h, int M, int b, const double* q2, double* Z, int ldz,
     if (ws_elems < q2_tile_ws_elems(M, b)) return GEP_ERR_ALLOC;
     const int W = 2 * TQ * b;
     const int nJ = Q / TQ + 1;
-    double* U = ws;
+    double* Ubuf = ws;
     double* Tmp = ws + rr((size_t)(Q / TQ + 1) * W * W);
     size_t smem = q2_tile_smem_bytes(b);
-    static unsigned long long attr_devices = 0;
-    if (first_use_on_device(attr_devices))
-      GEP_CUDA(cudaFuncSetAttribute(k_q2_tile_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)q2_tile_smem_bytes(BMAX)));
+    GEP_CHECK(set_tile_build_attr());
     for (int J = nJ - 1; J >= 0; --J) {
       const int nK = (Q - J * TQ) / TQ + 1;  // tiles (J, K) with a diamond: K TQ <= Q - J TQ
-      k_q2_tile_build<<<dim3(nK, (W + TB_COLS - 1) / TB_COLS), 256, smem, h->stream>>>(M, b, Q, J, q2, U,
-                                                                                      h->d_status);
-      GEP_CHECK(check_launch(h));
+      const double* U = Ubuf;
+      if (U_all) {
+        U = U_all + all_tiles_offset(Q, J) * (size_t)W * W;
+      } else {
+        k_q2_tile_build<<<dim3(nK, (W + TB_COLS - 1) / TB_COLS), 256, smem, h->stream>>>(M, b, Q, J, q2, Ubuf,
+                                                                                        h->d_status);
+        GEP_CHECK(check_launch(h));
+      }
       for (int K = 0; K < nK; ++K) {
         const int r0 = 1 + (J + K) * TQ * b;
         if (r0 >= M) break;

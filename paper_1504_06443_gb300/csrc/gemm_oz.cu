@@ -2,17 +2,20 @@
 // cores of sm_103a (tcgen05 + TMEM + TMA), by exact splitting of the operands.
 //
 // Splitting (per K panel): every row i of op(A) is scaled by 2^-e_i with
-// max_k |A_ik| < 2^e_i and cut into S signed 7-bit digits,
-//     A_ik 2^-e_i = sum_s d_s 2^-7s + r,   d_1 in [-128,128], d_s in [-64,64],
+// max_k |A_ik| < 2^(e_i - 1) and cut into S signed 7-bit digits,
+//     A_ik 2^-e_i = sum_s d_s 2^-7s + r,   every d_s in [-64,64],
+// (the FP32-grade setting keeps max_k |A_ik| < 2^e_i, its leading digit in [-128,128]),
 // each digit an integer held exactly in BF16; likewise every column j of op(B)
 // with 2^-f_j.  Then
 //     (op(A) op(B))_ij = 2^(e_i+f_j) sum_l 2^-7l L_l,   L_l = sum_{s+t=l} D^A_s D^B_t,
 // and only levels l <= LMAX are kept.  With S = 8 planes and LMAX = 9 (36 plane
 // products, the FP64 setting) the dropped levels and the digit remainders sit
-// near 2^-55 of the row/column scale; S = 3, LMAX = 4 (6 products) is the
+// near 2^-54 of the row/column scale; S = 3, LMAX = 4 (6 products) is the
 // FP32-grade setting of the mixed-precision path.  Each L_l is an integer
-// matrix product: over a 256-deep K chunk every partial sum stays below 2^24 in
-// magnitude, so the FP32 accumulation in tensor memory is exact.  After each
+// matrix product: with balanced leading digits a digit product is at most 2^12 in
+// magnitude and a level holds at most 8 of them (the FP32-grade levels at most
+// 2^13 + 2^12 + 2^13), so over a 512-deep K chunk every partial sum stays within 2^24
+// and the FP32 accumulation in tensor memory is exact.  After each
 // chunk the level sums are drained from TMEM into two 64-bit integer fixed-point
 // accumulators per output (levels 2..4 and 5..LMAX); FP64 arithmetic appears only
 // once per output element, in the final epilogue.
@@ -35,7 +38,7 @@
 namespace gep {
 namespace {
 
-constexpr int TM = 128, TN = 64, TK = 32, KCH = 256, STAGES = 2, MAXS = 8;
+constexpr int TM = 128, TN = 64, TK = 32, KCH = 512, STAGES = 2, MAXS = 8;
 constexpr int NTHREADS = 320;
 constexpr int KP_MAX = 4096;  // K panel per launch (integer accumulators sized for <= 16 chunks)
 
@@ -48,10 +51,16 @@ constexpr int KP_MAX = 4096;  // K panel per launch (integer accumulators sized 
 // Biased exponent field of |x| (0 for zero / subnormal).
 __device__ __forceinline__ int exp_field(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
 
-// e[r] with max_kk |X(r,kk)| < 2^e[r] (0 for an all-zero row); X(r,kk) = X[r*sr + kk*sk].
-// For a normal x with biased exponent E, |x| < 2^(E-1022).
+// Row scale exponent from the largest biased exponent m of the row: e with max |x| < 2^(e-1)
+// when xbit = 1 (for a normal x with biased exponent E, |x| < 2^(E-1022)), so that the
+// leading digit lies in [-64, 64] like the others; xbit = 0 (the FP32-grade setting, whose
+// few levels stay exact with a leading digit in [-128, 128]) keeps max |x| < 2^e.  0 for an
+// all-zero row.
+__device__ __forceinline__ int scale_exp(int m, int xbit) { return m ? m - 1022 + xbit : 0; }
+
+// e[r] = scale_exp of row r; X(r,kk) = X[r*sr + kk*sk].
 __global__ void k_rowexp(int R, int K, const double* __restrict__ X, long long sr, long long sk, int* __restrict__ e,
-                         const int* st) {
+                         const int* st, int xbit) {
   if (status_bad(st)) return;
   if (sk == 1) {  // warp per row, contiguous along kk
     int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -59,23 +68,52 @@ __global__ void k_rowexp(int R, int K, const double* __restrict__ X, long long s
     int m = 0;
     for (int kk = lane; kk < K; kk += 32) m = max(m, exp_field(X[r * sr + kk]));
     for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) e[r] = m ? m - 1022 : 0;
+    if (lane == 0) e[r] = scale_exp(m, xbit);
   } else {  // thread per row, consecutive rows contiguous
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     int m = 0;
     for (int kk = 0; kk < K; ++kk) m = max(m, exp_field(X[r + kk * sk]));
-    e[r] = m ? m - 1022 : 0;
+    e[r] = scale_exp(m, xbit);
   }
 }
 
-// Exact BF16 bit pattern of a small integer d (|d| <= 256).
-__device__ __forceinline__ unsigned short bf16_of_int(int d) {
-  if (d == 0) return 0;
-  unsigned a = (unsigned)(d < 0 ? -d : d);
-  int p = 31 - __clz((int)a);
-  unsigned mant = (a << (7 - p)) & 0x7Fu;
-  return (unsigned short)(((d < 0) ? 0x8000u : 0u) | ((unsigned)(127 + p) << 7) | mant);
+// Exact BF16 bit pattern of a small integer d (|d| <= 256): 1.5 * 2^23 + d is a float of
+// the binade [2^23, 2^24) whose last bits are d, so subtracting 1.5 * 2^23 gives d exactly
+// as an FP32 value, and with at most 9 significant bits its upper half is its BF16 pattern.
+__device__ __forceinline__ unsigned bf16_of_int(int d) {
+  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+  return (unsigned)__float_as_int(f) >> 16;
+}
+
+// Balanced base-128 digits of the fixed-point integer F (|F| < 2^(7S)), least significant
+// first: d_S..d_2 in [-64, 63], the leading d_1 what remains.  32-bit integer arithmetic
+// only: for S > 4 the low 28 bits give four digits and their carry joins the upper part.
+template <int S>
+__device__ __forceinline__ void digits_of(long long F, int* d) {
+  int v;
+  int q = S - 1;  // index of the next digit to produce (d[0] = d_1)
+  if (S > 4) {
+    int lo = (int)(F & 0x0FFFFFFFll);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int x = lo & 127;
+      x -= (x >= 64) ? 128 : 0;
+      lo = (lo - x) >> 7;
+      d[q--] = x;
+    }
+    v = (int)(F >> 28) + lo;
+  } else {
+    v = (int)F;
+  }
+#pragma unroll
+  for (int u = 0; u < (S > 4 ? S - 5 : S - 1); ++u) {
+    int x = v & 127;
+    x -= (x >= 64) ? 128 : 0;
+    v = (v - x) >> 7;
+    d[q--] = x;
+  }
+  d[0] = v;
 }
 
 // F = round(x 2^(7S - e)) as a signed integer (|F| < 2^(7S)), from the IEEE bits.
@@ -101,35 +139,39 @@ __device__ __forceinline__ long long to_fixed(double x, int e, int S) {
 
 // Digits of 4 consecutive elements x[0..3] of row r (columns kk .. kk+3, all < Kpad;
 // columns >= K are zero) written as one 8-byte store per plane.
-__device__ __forceinline__ void split4_store(const double* x, int kk, int K, int e, int S, size_t base,
-                                             size_t plane, unsigned short* __restrict__ out) {
-  long long F[4];
+template <int SC>
+__device__ __forceinline__ void split4_store_t(const double* x, int kk, int K, int e, size_t base, size_t plane,
+                                               unsigned short* __restrict__ out) {
+  int d[4][SC];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) F[u] = (kk + u < K) ? to_fixed(x[u], e, S) : 0ll;
-  for (int s = S - 1; s >= 1; --s) {
-    unsigned short b[4];
+  for (int u = 0; u < 4; ++u) digits_of<SC>((kk + u < K) ? to_fixed(x[u], e, SC) : 0ll, d[u]);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      int d = (int)(F[u] & 127);
-      if (d >= 64) d -= 128;
-      F[u] = (F[u] - d) >> 7;
-      b[u] = bf16_of_int(d);
-    }
+  for (int s = 0; s < SC; ++s) {
     uint2 w;
-    w.x = (unsigned)b[0] | ((unsigned)b[1] << 16);
-    w.y = (unsigned)b[2] | ((unsigned)b[3] << 16);
+    w.x = bf16_of_int(d[0][s]) | (bf16_of_int(d[1][s]) << 16);
+    w.y = bf16_of_int(d[2][s]) | (bf16_of_int(d[3][s]) << 16);
     *reinterpret_cast<uint2*>(out + base + (size_t)s * plane) = w;
   }
-  uint2 w;
-  w.x = (unsigned)bf16_of_int((int)F[0]) | ((unsigned)bf16_of_int((int)F[1]) << 16);
-  w.y = (unsigned)bf16_of_int((int)F[2]) | ((unsigned)bf16_of_int((int)F[3]) << 16);
-  *reinterpret_cast<uint2*>(out + base) = w;
+}
+
+__device__ __forceinline__ void split4_store(const double* x, int kk, int K, int e, int S, size_t base,
+                                             size_t plane, unsigned short* __restrict__ out) {
+  switch (S) {
+    case 8: split4_store_t<8>(x, kk, K, e, base, plane, out); break;
+    case 3: split4_store_t<3>(x, kk, K, e, base, plane, out); break;
+    case 1: split4_store_t<1>(x, kk, K, e, base, plane, out); break;
+    case 2: split4_store_t<2>(x, kk, K, e, base, plane, out); break;
+    case 4: split4_store_t<4>(x, kk, K, e, base, plane, out); break;
+    case 5: split4_store_t<5>(x, kk, K, e, base, plane, out); break;
+    case 6: split4_store_t<6>(x, kk, K, e, base, plane, out); break;
+    default: split4_store_t<7>(x, kk, K, e, base, plane, out); break;
+  }
 }
 
 // Digit planes out[s][r][kk] (bf16, kk contiguous, Kpad columns, zero padding).
-// x 2^-e[r] is rounded to the integer F = round(x 2^(7S-e)) (|F| < 2^(7S)), whose
+// x 2^-e[r] is rounded to the integer F = round(x 2^(7S-e)) (|F| <= 2^(7S-1)), whose
 // balanced base-128 digits are peeled off from the least significant end:
-// d_S..d_2 in [-64, 63], the leading d_1 in [-128, 128].  Plane s-1 holds d_s.
+// d_S..d_2 in [-64, 63], the leading d_1 in [-64, 64].  Plane s-1 holds d_s.
 __global__ void __launch_bounds__(256) k_split(int R, int K, int Kpad, const double* __restrict__ X, long long sr,
                                                long long sk, const int* __restrict__ e, int S,
                                                unsigned short* __restrict__ out, const int* st) {
@@ -156,6 +198,30 @@ __global__ void __launch_bounds__(256) k_split(int R, int K, int Kpad, const dou
   }
 }
 
+// Exponent pass and digit split in one kernel for an operand whose K runs contiguously
+// along each row (sk = 1): one warp per row, lane l taking columns 4 l + 128 i .. + 3; the
+// row is read twice (largest exponent, then digits), the second time from cache.
+__global__ void __launch_bounds__(256) k_split_rows(int R, int K, int Kpad, const double* __restrict__ X,
+                                                    long long sr, int* __restrict__ e_out, int S, int xbit,
+                                                    unsigned short* __restrict__ out, const int* st) {
+  if (status_bad(st)) return;
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (r >= R) return;
+  const double* x = X + (size_t)r * sr;
+  int m = 0;
+  for (int kk = lane; kk < K; kk += 32) m = max(m, exp_field(x[kk]));
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const int e = scale_exp(m, xbit);
+  if (lane == 0) e_out[r] = e;
+  const size_t plane = (size_t)R * Kpad;
+  for (int k0 = 4 * lane; k0 < Kpad; k0 += 128) {
+    double v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = (k0 + u < K) ? x[k0 + u] : 0.0;
+    split4_store(v, k0, K, e, S, (size_t)r * Kpad + k0, plane, out);
+  }
+}
+
 // Symmetric operand given by its lower triangle (op(A) = A, A(i, kk) = C(max, min)), K
 // panel [kb, kb + kc): exponents in two passes (the part of row i left of the diagonal,
 // read down the rows; then the part of column i below it, read along the column), and
@@ -173,7 +239,7 @@ __global__ void k_rowexp_sym_row(int R, int kb, int kc, const double* __restrict
 }
 
 __global__ void k_rowexp_sym_col(int R, int kb, int kc, const double* __restrict__ C, long long ldc,
-                                 int* __restrict__ e, const int* st) {
+                                 int* __restrict__ e, const int* st, int xbit) {
   if (status_bad(st)) return;
   int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (r >= R) return;
@@ -182,7 +248,7 @@ __global__ void k_rowexp_sym_col(int R, int kb, int kc, const double* __restrict
   for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (lane == 0) {
     m = max(m, e[r]);
-    e[r] = m ? m - 1022 : 0;
+    e[r] = scale_exp(m, xbit);
   }
 }
 
@@ -667,6 +733,8 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
     cudaFuncSetAttribute(k_oz_gemm<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes_for(MAXS));
   }
   int lower = (uplo == 'L' || uplo == 'l');
+  // balanced leading digits where a level may hold up to 8 digit products (see the top)
+  const int xbit = levels >= 8 ? 1 : 0;
   for (int kb = 0; kb < k; kb += KP) {
     int kc = min(KP, k - kb);
     int kpad = (kc + TK - 1) / TK * TK;
@@ -679,28 +747,32 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
     int* eb = ea + m;
     const double* Ap = A + (size_t)kb * ska;
     const double* Bp = B + (size_t)kb * skb;
+    // operands whose K is contiguous take the fused exponent-and-split kernel; the others
+    // (K strided) an exponent pass down the rows, then the tile-transposing split
     if (SA) {
       GEP_CUDA(cudaMemsetAsync(ea, 0, sizeof(int) * (size_t)m, h->stream));
       k_rowexp_sym_row<<<dim3((m + 255) / 256, (kc + 63) / 64), 256, 0, h->stream>>>(m, kb, kc, A, lda, ea,
                                                                                     h->d_status);
       GEP_CHECK(check_launch(h));
-      k_rowexp_sym_col<<<(m * 32 + 255) / 256, 256, 0, h->stream>>>(m, kb, kc, A, lda, ea, h->d_status);
-    } else if (ska == 1) {
-      k_rowexp<<<(m * 32 + 255) / 256, 256, 0, h->stream>>>(m, kc, Ap, sra, ska, ea, h->d_status);
-    } else {
-      k_rowexp<<<(m + 255) / 256, 256, 0, h->stream>>>(m, kc, Ap, sra, ska, ea, h->d_status);
-    }
-    GEP_CHECK(check_launch(h));
-    if (skb == 1) k_rowexp<<<(n * 32 + 255) / 256, 256, 0, h->stream>>>(n, kc, Bp, srb, skb, eb, h->d_status);
-    else k_rowexp<<<(n + 255) / 256, 256, 0, h->stream>>>(n, kc, Bp, srb, skb, eb, h->d_status);
-    GEP_CHECK(check_launch(h));
-    if (SA)
+      k_rowexp_sym_col<<<(m * 32 + 255) / 256, 256, 0, h->stream>>>(m, kb, kc, A, lda, ea, h->d_status, xbit);
+      GEP_CHECK(check_launch(h));
       k_split_sym<<<dim3(kpad / 32, (m + 31) / 32), 256, 0, h->stream>>>(m, kc, kpad, kb, A, lda, ea, S, As,
                                                                          h->d_status);
-    else
+    } else if (ska == 1) {
+      k_split_rows<<<(m * 32 + 255) / 256, 256, 0, h->stream>>>(m, kc, kpad, Ap, sra, ea, S, xbit, As, h->d_status);
+    } else {
+      k_rowexp<<<(m + 255) / 256, 256, 0, h->stream>>>(m, kc, Ap, sra, ska, ea, h->d_status, xbit);
+      GEP_CHECK(check_launch(h));
       k_split<<<dim3(kpad / 32, (m + 31) / 32), 256, 0, h->stream>>>(m, kc, kpad, Ap, sra, ska, ea, S, As, h->d_status);
+    }
     GEP_CHECK(check_launch(h));
-    k_split<<<dim3(kpad / 32, (n + 31) / 32), 256, 0, h->stream>>>(n, kc, kpad, Bp, srb, skb, eb, S, Bs, h->d_status);
+    if (skb == 1) {
+      k_split_rows<<<(n * 32 + 255) / 256, 256, 0, h->stream>>>(n, kc, kpad, Bp, srb, eb, S, xbit, Bs, h->d_status);
+    } else {
+      k_rowexp<<<(n + 255) / 256, 256, 0, h->stream>>>(n, kc, Bp, srb, skb, eb, h->d_status, xbit);
+      GEP_CHECK(check_launch(h));
+      k_split<<<dim3(kpad / 32, (n + 31) / 32), 256, 0, h->stream>>>(n, kc, kpad, Bp, srb, skb, eb, S, Bs, h->d_status);
+    }
     GEP_CHECK(check_launch(h));
     CUtensorMap mA, mB;
     GEP_CHECK(encode_map(&mA, As, kpad, m, S, TM));

@@ -29,6 +29,10 @@ struct gep_handle_s {
   int magic = 0x6e70;
   cudaEvent_t ev[8] = {};
   cudaEvent_t ev_band = nullptr;  // between full->band and bulge chasing (two-stage, timers on)
+  // second stream of the solve: the dense Q2 tiles are built there while the tridiagonal
+  // eigensolver runs on the handle's stream (fork/join by events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool band_recorded = false;
   bool timers_recorded = false;
   // optional per-launch timing of the tensor-core product kernel
@@ -169,7 +173,10 @@ int band_to_tridiag(gep_handle_t h, int M, const double* C, int ldc, int b, doub
                     double* ws, size_t ws_elems);
 size_t q2_tile_ws_elems(int M, int b);
 int apply_q2(gep_handle_t h, int M, int b, const double* q2, double* Z, int ldz, int ncol, int engine, double* ws,
-             size_t ws_elems);
+             size_t ws_elems, const double* U_all = nullptr);
+// every dense Q2 tile at once (tensor-core engines), e.g. on a second stream
+size_t q2_all_tiles_elems(int M, int b);
+int build_q2_tiles(gep_handle_t h, cudaStream_t stream, int M, int b, const double* q2, double* U);
 size_t backtransform_ws_elems(int M, int ncol);
 int tridiag_eig_dc(gep_handle_t h, int M, const double* d, const double* e, double* w, double* Z,
                    int ldz, double* ws, size_t ws_elems, int engine);
