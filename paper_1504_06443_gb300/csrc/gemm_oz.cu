@@ -58,24 +58,22 @@ __device__ __forceinline__ int exp_field(double x) { return (int)((__double_as_l
 // all-zero row.
 __device__ __forceinline__ int scale_exp(int m, int xbit) { return m ? m - 1022 + xbit : 0; }
 
-// e[r] = scale_exp of row r; X(r,kk) = X[r*sr + kk*sk].
-__global__ void k_rowexp(int R, int K, const double* __restrict__ X, long long sr, long long sk, int* __restrict__ e,
-                         const int* st, int xbit) {
+// The exponent arrays of the engine hold, per row of op(A) and per column of op(B), the
+// largest biased exponent field of the K panel (raw); scale_exp turns it into the scale.
+//
+// raw[r] = max over the K panel of exp_field(X(r, kk)), X(r,kk) = X[r*sr + kk*sk], for an
+// operand whose K is strided (consecutive rows contiguous): block (256 rows, one 128-deep
+// slab of K), atomicMax into raw (zero on entry), so that short-and-wide panels spread over
+// many CTAs.
+__global__ void k_rowexp_slab(int R, int K, const double* __restrict__ X, long long sr, long long sk,
+                              int* __restrict__ raw, const int* st) {
   if (status_bad(st)) return;
-  if (sk == 1) {  // warp per row, contiguous along kk
-    int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (r >= R) return;
-    int m = 0;
-    for (int kk = lane; kk < K; kk += 32) m = max(m, exp_field(X[r * sr + kk]));
-    for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) e[r] = scale_exp(m, xbit);
-  } else {  // thread per row, consecutive rows contiguous
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= R) return;
-    int m = 0;
-    for (int kk = 0; kk < K; ++kk) m = max(m, exp_field(X[r + kk * sk]));
-    e[r] = scale_exp(m, xbit);
-  }
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const int k0 = blockIdx.y * 128, k1 = min(K, k0 + 128);
+  int m = 0;
+  for (int kk = k0; kk < k1; ++kk) m = max(m, exp_field(X[r * sr + kk * sk]));
+  if (m) atomicMax(raw + r, m);
 }
 
 // Exact BF16 bit pattern of a small integer d (|d| <= 256): 1.5 * 2^23 + d is a float of
@@ -173,7 +171,7 @@ __device__ __forceinline__ void split4_store(const double* x, int kk, int K, int
 // balanced base-128 digits are peeled off from the least significant end:
 // d_S..d_2 in [-64, 63], the leading d_1 in [-64, 64].  Plane s-1 holds d_s.
 __global__ void __launch_bounds__(256) k_split(int R, int K, int Kpad, const double* __restrict__ X, long long sr,
-                                               long long sk, const int* __restrict__ e, int S,
+                                               long long sk, const int* __restrict__ e, int S, int xbit,
                                                unsigned short* __restrict__ out, const int* st) {
   __shared__ double t[32][33];
   if (status_bad(st)) return;
@@ -193,7 +191,7 @@ __global__ void __launch_bounds__(256) k_split(int R, int K, int Kpad, const dou
     const int r = r0 + q;
     if (r < R) {
       double x[4] = {t[q][c4], t[q][c4 + 1], t[q][c4 + 2], t[q][c4 + 3]};
-      split4_store(x, k0 + c4, K, e[r], S, (size_t)r * Kpad + k0 + c4, (size_t)R * Kpad, out);
+      split4_store(x, k0 + c4, K, scale_exp(e[r], xbit), S, (size_t)r * Kpad + k0 + c4, (size_t)R * Kpad, out);
     }
   }
 }
@@ -212,7 +210,7 @@ __global__ void __launch_bounds__(256) k_split_rows(int R, int K, int Kpad, cons
   for (int kk = lane; kk < K; kk += 32) m = max(m, exp_field(x[kk]));
   for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   const int e = scale_exp(m, xbit);
-  if (lane == 0) e_out[r] = e;
+  if (lane == 0) e_out[r] = m;
   const size_t plane = (size_t)R * Kpad;
   for (int k0 = 4 * lane; k0 < Kpad; k0 += 128) {
     double v[4];
@@ -239,7 +237,7 @@ __global__ void k_rowexp_sym_row(int R, int kb, int kc, const double* __restrict
 }
 
 __global__ void k_rowexp_sym_col(int R, int kb, int kc, const double* __restrict__ C, long long ldc,
-                                 int* __restrict__ e, const int* st, int xbit) {
+                                 int* __restrict__ e, const int* st) {
   if (status_bad(st)) return;
   int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (r >= R) return;
@@ -247,13 +245,12 @@ __global__ void k_rowexp_sym_col(int R, int kb, int kc, const double* __restrict
   for (int kk = max(r + 1, kb) + lane; kk < kb + kc; kk += 32) m = max(m, exp_field(C[kk + r * ldc]));
   for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (lane == 0) {
-    m = max(m, e[r]);
-    e[r] = scale_exp(m, xbit);
+    e[r] = max(m, e[r]);
   }
 }
 
 __global__ void __launch_bounds__(256) k_split_sym(int R, int K, int Kpad, int kb, const double* __restrict__ C,
-                                                   long long ldc, const int* __restrict__ e, int S,
+                                                   long long ldc, const int* __restrict__ e, int S, int xbit,
                                                    unsigned short* __restrict__ out, const int* st) {
   __shared__ double t[32][33];
   if (status_bad(st)) return;
@@ -277,7 +274,7 @@ __global__ void __launch_bounds__(256) k_split_sym(int R, int K, int Kpad, int k
     const int r = r0 + q;
     if (r < R) {
       double x[4] = {t[q][c4], t[q][c4 + 1], t[q][c4 + 2], t[q][c4 + 3]};
-      split4_store(x, k0 + c4, K, e[r], S, (size_t)r * Kpad + k0 + c4, (size_t)R * Kpad, out);
+      split4_store(x, k0 + c4, K, scale_exp(e[r], xbit), S, (size_t)r * Kpad + k0 + c4, (size_t)R * Kpad, out);
     }
   }
 }
@@ -450,7 +447,7 @@ __device__ __forceinline__ double fixed_to_double(long long hi, long long lo, in
 constexpr int GROUP_M = 8;  // row tiles per group of the tile order (L2 reuse of the A planes)
 
 struct OzArgs {
-  int m, n, kpad, S, lmax, lower;
+  int m, n, kpad, S, lmax, lower, xbit;
   int gx, gy, ntiles;  // tile grid gx x gy (128-row x 64-column tiles), in grouped order
   const int* ea;
   const int* eb;
@@ -629,7 +626,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__
       if (lane == 0) mbar_arrive(bar_acce);
     }
     if (ok && row < p.m) {
-      const int ea = p.ea[row];
+      const int ea = scale_exp(p.ea[row], p.xbit);
       const bool two = LMAX >= 5;  // a second (low) accumulator is in use
       const int D = two ? 7 * LMAX - 28 : 0;
       const int base_adj = ea - (two ? 7 * LMAX : 28);
@@ -638,7 +635,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__
       for (int j = 0; j < 32; ++j) {
         int col = tn + half * 32 + j;
         if (col >= p.n || (p.lower && row < col)) continue;
-        double v = fixed_to_double(hi[j], two ? lo[j] : 0ll, D, base_adj + p.eb[col]);
+        double v = fixed_to_double(hi[j], two ? lo[j] : 0ll, D, base_adj + scale_exp(p.eb[col], p.xbit));
         double* cp = p.C + (size_t)row + (size_t)col * p.ldc;
         double out = (alpha == 1.0) ? v : (alpha == -1.0 ? -v : alpha * v);
         if (beta != 0.0) out = fma(beta, *cp, out);
@@ -754,31 +751,37 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
       k_rowexp_sym_row<<<dim3((m + 255) / 256, (kc + 63) / 64), 256, 0, h->stream>>>(m, kb, kc, A, lda, ea,
                                                                                     h->d_status);
       GEP_CHECK(check_launch(h));
-      k_rowexp_sym_col<<<(m * 32 + 255) / 256, 256, 0, h->stream>>>(m, kb, kc, A, lda, ea, h->d_status, xbit);
+      k_rowexp_sym_col<<<(m * 32 + 255) / 256, 256, 0, h->stream>>>(m, kb, kc, A, lda, ea, h->d_status);
       GEP_CHECK(check_launch(h));
-      k_split_sym<<<dim3(kpad / 32, (m + 31) / 32), 256, 0, h->stream>>>(m, kc, kpad, kb, A, lda, ea, S, As,
+      k_split_sym<<<dim3(kpad / 32, (m + 31) / 32), 256, 0, h->stream>>>(m, kc, kpad, kb, A, lda, ea, S, xbit, As,
                                                                          h->d_status);
     } else if (ska == 1) {
       k_split_rows<<<(m * 32 + 255) / 256, 256, 0, h->stream>>>(m, kc, kpad, Ap, sra, ea, S, xbit, As, h->d_status);
     } else {
-      k_rowexp<<<(m + 255) / 256, 256, 0, h->stream>>>(m, kc, Ap, sra, ska, ea, h->d_status, xbit);
+      GEP_CUDA(cudaMemsetAsync(ea, 0, sizeof(int) * (size_t)m, h->stream));
+      k_rowexp_slab<<<dim3((m + 255) / 256, (kc + 127) / 128), 256, 0, h->stream>>>(m, kc, Ap, sra, ska, ea,
+                                                                                   h->d_status);
       GEP_CHECK(check_launch(h));
-      k_split<<<dim3(kpad / 32, (m + 31) / 32), 256, 0, h->stream>>>(m, kc, kpad, Ap, sra, ska, ea, S, As, h->d_status);
+      k_split<<<dim3(kpad / 32, (m + 31) / 32), 256, 0, h->stream>>>(m, kc, kpad, Ap, sra, ska, ea, S, xbit, As,
+                                                                     h->d_status);
     }
     GEP_CHECK(check_launch(h));
     if (skb == 1) {
       k_split_rows<<<(n * 32 + 255) / 256, 256, 0, h->stream>>>(n, kc, kpad, Bp, srb, eb, S, xbit, Bs, h->d_status);
     } else {
-      k_rowexp<<<(n + 255) / 256, 256, 0, h->stream>>>(n, kc, Bp, srb, skb, eb, h->d_status, xbit);
+      GEP_CUDA(cudaMemsetAsync(eb, 0, sizeof(int) * (size_t)n, h->stream));
+      k_rowexp_slab<<<dim3((n + 255) / 256, (kc + 127) / 128), 256, 0, h->stream>>>(n, kc, Bp, srb, skb, eb,
+                                                                                   h->d_status);
       GEP_CHECK(check_launch(h));
-      k_split<<<dim3(kpad / 32, (n + 31) / 32), 256, 0, h->stream>>>(n, kc, kpad, Bp, srb, skb, eb, S, Bs, h->d_status);
+      k_split<<<dim3(kpad / 32, (n + 31) / 32), 256, 0, h->stream>>>(n, kc, kpad, Bp, srb, skb, eb, S, xbit, Bs,
+                                                                     h->d_status);
     }
     GEP_CHECK(check_launch(h));
     CUtensorMap mA, mB;
     GEP_CHECK(encode_map(&mA, As, kpad, m, S, TM));
     GEP_CHECK(encode_map(&mB, Bs, kpad, n, S, TN));
     OzArgs a;
-    a.m = m; a.n = n; a.kpad = kpad; a.S = S; a.lmax = levels; a.lower = lower;
+    a.m = m; a.n = n; a.kpad = kpad; a.S = S; a.lmax = levels; a.lower = lower; a.xbit = xbit;
     a.ea = ea; a.eb = eb; a.alpha = alpha; a.beta = (kb == 0) ? beta : 1.0; a.C = C; a.ldc = ldc; a.st = h->d_status;
     const int gx = (m + TM - 1) / TM, gy = (n + TN - 1) / TN;
     a.gx = gx;
