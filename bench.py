@@ -44,6 +44,9 @@ def parse():
     p.add_argument("--values-only", action="store_true", help="eigenvalues only (T_evo of the paper's benchmark)")
     p.add_argument("--cpu-sample-M", type=int, nargs="+", default=[1024, 2048, 3072],
                    help="orders of the oracle solves the c M^3 fit of the CPU baseline is taken over")
+    p.add_argument("--profile-solve", action="store_true",
+                   help="one untimed solve of the pencil with the given options and exit (profiling aid: "
+                        "the command ncu launch lists and kernel captures of whole solves run)")
     p.add_argument("--peaks", action="store_true",
                    help="measure the FP64 peaks of this GPU (cuBLAS DGEMM burst and sustained) and exit")
     p.add_argument("--no-e2e", action="store_true")
@@ -466,6 +469,25 @@ def fp64_peaks(n=8192, burst_reps=5, sustained_s=3.0):
                    f"{reps} back to back (sustained), CUDA events"}
 
 
+def run_profile_solve(a):
+    """One solve of the tight-binding pencil of order --M (seed --seed) with the bench's solver
+    options, synchronised, nothing timed: the command ncu launch lists and kernel captures of a
+    whole solve run."""
+    import torch
+    import gep_inputs as gi
+    from paper_1504_06443_gb300 import build as gbuild
+    import paper_1504_06443_gb300 as gep
+    gbuild.build()
+    tb = gi.tight_binding(a.M, a.seed)
+    A = torch.as_tensor(tb["A"], device="cuda")
+    B = torch.as_tensor(tb["B"], device="cuda")
+    w, Y, info = gep.solve(A, B, reducer=a.reducer, sep=a.sep, bandwidth=a.bandwidth, precision=a.precision,
+                           want_vectors=not a.values_only, timers=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_solve": a.M, "info": info, "stage_ms": [round(x, 2) for x in
+                                                                       gep.default_handle().stage_times()]}))
+
+
 def run_peaks(a):
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -478,8 +500,8 @@ def run_peaks(a):
 # (profiles/k_oz_gemm_4096x4096x4096.md: dram__bytes_read.sum + dram__bytes_write.sum of one
 # 4096^3 launch, 36 plane products).  It is scaled to the timed launches by their tensor
 # flops and reported only while the kernel source is the one that was captured.
-OZ_CAPTURE = {"dram_bytes": 4.072e9 + 0.142e9, "tensor_flops": 36 * 2.0 * 4096 ** 3,
-              "kernel_sha1": "b0b9d816fcb173c9c1bacf2c80c1113bd6c532a2",
+OZ_CAPTURE = {"dram_bytes": 2.209185e9 + 0.137576e9, "tensor_flops": 36 * 2.0 * 4096 ** 3,
+              "kernel_sha1": "8618ccf918c49c175a1eb8cec40b496b2671a423",
               "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 4096^3 k_oz_gemm launch "
                       "(profiles/k_oz_gemm_4096x4096x4096.md), scaled to the average timed launch by its "
                       "tensor flops; null when the kernel source differs from the captured one"}
@@ -571,6 +593,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if a.peaks:
         run_peaks(a)
+        return
+    if a.profile_solve:
+        run_profile_solve(a)
         return
     if a.gemm:
         run_gemm(a)
