@@ -164,6 +164,7 @@ def run_batched(a):
     reps = [next(i for i, M in enumerate(orders) if gep._bucket(M) == b) for b in sorted({gep._bucket(M) for M in orders})]
     tuner = gep.Autotuner()
     choice = tuner.tune([As[i] for i in reps], [Bs[i] for i in reps], reps=1)
+    small = tuner.tune_small(As, Bs)
     precs = [tuner.precision_for(M) for M in orders]
     flops = sum(7.0 * float(M) ** 3 for M in orders)
     # looping single solves on one stream (baseline)
@@ -175,7 +176,7 @@ def run_batched(a):
     e1.record()
     torch.cuda.synchronize()
     loop_s = e0.elapsed_time(e1) / 1e3
-    bs = gep.BatchedSolver(As, Bs, nstreams=16, precisions=precs)
+    bs = gep.BatchedSolver(As, Bs, nstreams=16, precisions=precs, batch_small=small)
     bs.capture()
     for _ in range(a.warmup):
         bs.replay()
@@ -210,6 +211,8 @@ def run_batched(a):
            "config": {"workload": f"{len(orders)} tight-binding pencils, M log-uniform in [64, 2048]",
                       "orders_min_max": [min(orders), max(orders)], "nstreams": 16, "graph": "one captured CUDA graph",
                       "autotuned_engine_per_bucket": {str(k): v for k, v in choice.items()},
+                      "one_cta_pencils_up_to": small,
+                      "n_one_cta_pencils": sum(1 for M in orders if M <= small),
                       "generator_s": round(gen_s, 1),
                       "parallelism": f"LPT shards of the batch over {world} ranks" if world > 1 else "single"}}
     print(json.dumps(out), flush=True)

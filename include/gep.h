@@ -56,9 +56,15 @@ typedef struct gep_handle_s* gep_handle_t;
                                   C = A' = D^-1/2 W^T A W D^-1/2, Y = W D^-1/2 Z          */
 
 /* SEP-solver variants (section 3.1: conventional tridiagonalisation, or
- * narrow-band reduction followed by band -> tridiagonal). */
+ * narrow-band reduction followed by band -> tridiagonal; section 6: the parallel
+ * block-Jacobi method named as future work). */
 #define GEP_SEP_1STAGE 0
 #define GEP_SEP_2STAGE 1
+#define GEP_SEP_JACOBI 2 /* block Jacobi on C itself (no tridiagonal form, no back-transformation
+                            of Householder reflectors): blocks of 32 columns, every pair of blocks
+                            diagonalised exactly by one CTA per round (round-robin order), the
+                            block rotations applied to C and to the eigenvectors; FP64 on the
+                            CUDA cores, about 8 M^3 flops per sweep.  Stage times: t[3] holds it. */
 
 /* Arithmetic of the dense contractions. */
 #define GEP_PREC_FP64 0          /* FP64 throughout                                     */
@@ -81,6 +87,10 @@ typedef struct gep_options {
                        T, and only the n_want wanted columns are back-transformed (Q2, Q1, Eq. 6
                        or Eq. 9 on n_want columns).  Not with GEP_PREC_MIXED_REFINED nor in
                        gep_solve_batched (GEP_ERR_UNSUPPORTED). */
+  int batch_small;  /* gep_solve_batched only: pencils of order <= batch_small (at most 128) are
+                       each solved whole by one CTA (Cholesky, C = L^-1 A L^-T, cyclic Jacobi,
+                       Y = L^-T Q, all FP64), all of them in one persistent launch that takes
+                       them from a device work queue, largest order first; 0 = none. */
 } gep_options;
 
 /* Fills *o with the defaults: TWOSIDED, 1STAGE, b = 0, FP64, vectors, no overwrite, no timers.
@@ -207,11 +217,12 @@ int gep_adjoint(gep_handle_t h, int M, int n_occ, const double* w, const double*
 
 /* ---- batched solves (many independent pencils of uneven order) -------------------
  * Solves count pencils (A_i, B_i) of order M[i] with the workflow of gep_solve; host
- * arrays of device pointers.  Work is spread over nstreams (1..64) concurrent child
- * streams (largest M^3 first, each to the least loaded stream), forked from and joined
- * back into the handle's stream with events, so the whole call can be captured into
- * one CUDA graph (call it once outside capture first: that call creates the child
- * streams and their status blocks).  precision[i] (may be NULL: o->precision for all)
+ * arrays of device pointers.  Pencils of order <= o->batch_small go to one persistent
+ * launch on the handle's stream (one CTA per pencil, see gep_options).  The others are
+ * spread over nstreams (1..64) concurrent child streams (largest M^3 first, each to the
+ * least loaded stream), forked from and joined back into the handle's stream with events,
+ * so the whole call can be captured into one CUDA graph (call it once outside capture
+ * first: that call creates the child streams and their status blocks).  precision[i] (may be NULL: o->precision for all)
  * selects the product engine per pencil (the autotuned choice per size bucket).
  * The workspace (gep_solve_batched_workspace_size) holds one solve workspace per
  * stream, sized for the largest pencil that stream receives.  Numerical status of

@@ -19,21 +19,21 @@ import threading
 
 __all__ = ["load", "solve", "solve_host", "cholesky", "reduce", "tridiag_1stage", "tridiag_eig",
            "sep_backtransform", "tridiag_2stage", "sep_backtransform_2stage", "gep_backtransform", "dgemm", "Handle", "default_handle",
-           "RED_TWOSIDED", "RED_EXPLICIT_INV", "RED_EIGENEXA", "SEP_1STAGE", "SEP_2STAGE", "PREC_FP64",
+           "RED_TWOSIDED", "RED_EXPLICIT_INV", "RED_EIGENEXA", "SEP_1STAGE", "SEP_JACOBI", "SEP_2STAGE", "PREC_FP64",
            "PREC_FP64_EMULATED", "PREC_MIXED_REFINED", "GepError", "shard_batch"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libgep.so")
 
 RED_TWOSIDED, RED_EXPLICIT_INV, RED_EIGENEXA = 0, 1, 2
-SEP_1STAGE, SEP_2STAGE = 0, 1
+SEP_1STAGE, SEP_2STAGE, SEP_JACOBI = 0, 1, 2
 PREC_FP64, PREC_FP64_EMULATED, PREC_MIXED_REFINED = 0, 1, 2
 # return codes of include/gep.h
 ERR_CUDA, ERR_ALLOC, ERR_NONFINITE, ERR_TIMEOUT, ERR_HANDLE, ERR_UNSUPPORTED, ERR_TOO_LARGE = (
     -100, -101, -102, -103, -104, -105, -106)
 
 _REDUCERS = {"twosided": RED_TWOSIDED, "explicit_inv": RED_EXPLICIT_INV, "eigenexa": RED_EIGENEXA}
-_SEPS = {"1stage": SEP_1STAGE, "2stage": SEP_2STAGE}
+_SEPS = {"1stage": SEP_1STAGE, "2stage": SEP_2STAGE, "jacobi": SEP_JACOBI}
 _PRECS = {"fp64": PREC_FP64, "fp64_emulated": PREC_FP64_EMULATED, "mixed_refined": PREC_MIXED_REFINED}
 
 
@@ -47,7 +47,8 @@ class GepError(RuntimeError):
 class GepOptions(ctypes.Structure):
     _fields_ = [("reducer", ctypes.c_int), ("sep", ctypes.c_int), ("bandwidth", ctypes.c_int),
                 ("precision", ctypes.c_int), ("want_vectors", ctypes.c_int), ("overwrite", ctypes.c_int),
-                ("timers", ctypes.c_int), ("refine_iters", ctypes.c_int), ("n_want", ctypes.c_int)]
+                ("timers", ctypes.c_int), ("refine_iters", ctypes.c_int), ("n_want", ctypes.c_int),
+                ("batch_small", ctypes.c_int)]
 
 
 _lib = None
@@ -316,7 +317,7 @@ def default_handle():
 
 
 def make_options(reducer="twosided", sep="1stage", precision="fp64", want_vectors=True, overwrite=False,
-                 timers=False, bandwidth=0, refine_iters=0, n_want=0):
+                 timers=False, bandwidth=0, refine_iters=0, n_want=0, batch_small=0):
     o = GepOptions()
     load().gep_default_options(ctypes.byref(o))
     o.reducer = _REDUCERS[reducer] if isinstance(reducer, str) else int(reducer)
@@ -328,6 +329,7 @@ def make_options(reducer="twosided", sep="1stage", precision="fp64", want_vector
     o.bandwidth = int(bandwidth)
     o.refine_iters = int(refine_iters)
     o.n_want = int(n_want)
+    o.batch_small = int(batch_small)
     return o
 
 
@@ -703,10 +705,39 @@ def _bucket(M):
 
 class Autotuner:
     """Per size bucket, the faster of the two FP64-accurate product engines (FP64 FMA
-    tiles or split-BF16 tensor-core tiles), timed on one pencil of the bucket."""
+    tiles or split-BF16 tensor-core tiles), timed on one pencil of the bucket; and, for the
+    pencils of order <= 128, whether solving each whole in one CTA of one persistent launch
+    (batch_small) beats the staged workflow on concurrent streams, timed on those pencils."""
 
     def __init__(self):
         self.choice = {}
+        self.batch_small = 0
+
+    def tune_small(self, As, Bs, nstreams=16, reps=1):
+        """Times the pencils of order <= 128 both ways (one-CTA persistent launch, staged
+        workflow with the tuned engines) and keeps the faster: sets self.batch_small."""
+        import time
+        torch = _torch()
+        pick = [i for i, a in enumerate(As) if int(a.shape[0]) <= 128]
+        if not pick:
+            self.batch_small = 0
+            return self.batch_small
+        sa, sb = [As[i] for i in pick], [Bs[i] for i in pick]
+        best, best_t = 0, None
+        for small in (128, 0):
+            bs = BatchedSolver(sa, sb, nstreams=nstreams, batch_small=small,
+                               precisions=[self.precision_for(int(a.shape[0])) for a in sa])
+            bs.run()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                bs.run()
+            torch.cuda.synchronize()
+            t = (time.perf_counter() - t0) / reps
+            if best_t is None or t < best_t:
+                best, best_t = small, t
+        self.batch_small = best
+        return best
 
     def tune(self, As, Bs, reps=2):
         import time
@@ -736,9 +767,11 @@ class Autotuner:
 class BatchedSolver:
     """Many independent pencils (A_i, B_i) solved by gep_solve_batched over `nstreams`
     concurrent streams; capture() records the whole batch into one CUDA graph that
-    replay() launches again (inputs are read from the same device buffers each time)."""
+    replay() launches again (inputs are read from the same device buffers each time).
+    batch_small > 0: pencils of order <= batch_small (at most 128) are solved whole by one
+    CTA each, all in one persistent launch."""
 
-    def __init__(self, As, Bs, nstreams=8, precision="fp64_emulated", precisions=None, handle=None):
+    def __init__(self, As, Bs, nstreams=8, precision="fp64_emulated", precisions=None, handle=None, batch_small=0):
         torch = _torch()
         if len(As) != len(Bs) or len(As) == 0:
             raise ValueError("As and Bs must be non-empty lists of the same length")
@@ -754,7 +787,7 @@ class BatchedSolver:
         dev = self.As[0].device
         self.w = [torch.empty(m, dtype=torch.float64, device=dev) for m in self.M]
         self.Yt = [torch.empty((m, m), dtype=torch.float64, device=dev) for m in self.M]
-        self.o = make_options(precision=precision)
+        self.o = make_options(precision=precision, batch_small=batch_small)
         self.nstreams = int(nstreams)
         n = self.count
         self._M = (ctypes.c_int * n)(*self.M)

@@ -23,6 +23,7 @@ constexpr int kDefaultBand = 64;  // bandwidth of the two-stage reduction when o
 
 int band_of(const gep_options* o) { return o->bandwidth > 0 ? o->bandwidth : kDefaultBand; }
 bool two_stage(const gep_options* o) { return o->sep == GEP_SEP_2STAGE; }
+bool jacobi(const gep_options* o) { return o->sep == GEP_SEP_JACOBI; }
 bool eigenexa(const gep_options* o) { return o->reducer == GEP_RED_EIGENEXA; }
 // the SEP solver runs with eigenvectors: for the caller's pencil, or on B (Eq. 7)
 bool sep_vectors(const gep_options* o) { return o->want_vectors || eigenexa(o); }
@@ -47,7 +48,9 @@ size_t union_bytes(int M, const gep_options* o) {
   size_t red = (o->reducer == GEP_RED_EXPLICIT_INV) ? r256(mm) + r256(mm) + r256(tmpb)
                : eigenexa(o) ? r256(mm)  // A X of Eq. 8
                              : r256(mm) + r256(tmpb);
-  size_t tri = two_stage(o) ? band_ws_elems(M, band_of(o)) * sizeof(double) : tridiag_ws_elems(M) * sizeof(double);
+  size_t tri = two_stage(o) ? band_ws_elems(M, band_of(o)) * sizeof(double)
+               : jacobi(o)  ? jacobi_ws_elems(M) * sizeof(double)
+                            : tridiag_ws_elems(M) * sizeof(double);
   size_t dc = sep_vectors(o) ? dc_ws_bytes(M) : 0;
   size_t bt = sep_vectors(o) ? backtransform_ws_elems(M, M) * sizeof(double) : 0;
   if (two_stage(o) && sep_vectors(o)) {
@@ -99,7 +102,7 @@ int check_opts(const gep_options* o) {
   if (!o) return -1;
   if (o->reducer != GEP_RED_TWOSIDED && o->reducer != GEP_RED_EXPLICIT_INV && o->reducer != GEP_RED_EIGENEXA)
     return GEP_ERR_UNSUPPORTED;
-  if (o->sep != GEP_SEP_1STAGE && o->sep != GEP_SEP_2STAGE) return GEP_ERR_UNSUPPORTED;
+  if (o->sep != GEP_SEP_1STAGE && o->sep != GEP_SEP_2STAGE && o->sep != GEP_SEP_JACOBI) return GEP_ERR_UNSUPPORTED;
   if (o->sep == GEP_SEP_2STAGE && (o->bandwidth < 0 || o->bandwidth > 64)) return GEP_ERR_UNSUPPORTED;
   if (o->precision != GEP_PREC_FP64 && o->precision != GEP_PREC_FP64_EMULATED &&
       o->precision != GEP_PREC_MIXED_REFINED)
@@ -132,6 +135,20 @@ int sep_solve(gep_handle_t h, int M, double* C, int ldc, const gep_options* o, d
               bool timed, int n = 0, double* Zt = nullptr, double* wt = nullptr, double* q2u = nullptr) {
   if (n <= 0 || n > M) n = M;
   const int bw = band_of(o);
+  if (jacobi(o)) {  // no tridiagonal form: the block-Jacobi solver works on C itself
+    if (timed) mark(h, o, 3);
+    double* wj = (n < M) ? wt : w;
+    double* Zj = (n < M) ? Zt : Z;
+    if (n < M && Z && (!Zt || !wt)) return GEP_ERR_ALLOC;
+    if (n < M && !Z && !wt) return GEP_ERR_ALLOC;
+    GEP_CHECK(jacobi_sep(h, M, C, ldc, wj, Zj, (n < M) ? M : ldz, (double*)uni));
+    if (n < M) {
+      GEP_CHECK(copy_matrix(h, n, 1, wt, n, w, n));
+      if (Z) GEP_CHECK(copy_matrix(h, M, n, Zt, M, Z, ldz));
+    }
+    if (timed) mark(h, o, 4);
+    return GEP_OK;
+  }
   if (two_stage(o)) {
     GEP_CHECK(band_reduce(h, M, C, ldc, bw, tvec, (double*)uni, uni_bytes / sizeof(double), eng));  // S1b
     if (timed && o->timers) cudaEventRecord(h->ev_band, h->stream);
@@ -224,6 +241,7 @@ int gep_destroy(gep_handle_t h) {
   }
   if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   cudaFree(h->d_batch_info);
+  cudaFree(h->d_small_next);
   for (int i = 0; i < 8; ++i) cudaEventDestroy(h->ev[i]);
   cudaEventDestroy(h->ev_band);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -806,14 +824,19 @@ constexpr int kMaxBatch = 4096;
 
 struct BatchPlan {
   int ns;
-  int assign[kMaxBatch];
-  size_t need[64], off[64], total;
+  int assign[kMaxBatch];  // child stream of pencil i, -1 for the one-CTA small-pencil launch
+  int small_order[kMaxBatch], nsmall, small_ctas;
+  size_t need[64], off[64], total, small_off;
 };
 
-int make_plan(int count, const int* M, const gep_options* o, const int* prec, int nstreams, BatchPlan* p) {
+int small_limit(const gep_options* o) { return o->batch_small < SMALL_MAX ? o->batch_small : SMALL_MAX; }
+
+int make_plan(gep_handle_t h, int count, const int* M, const gep_options* o, const int* prec, int nstreams,
+              BatchPlan* p) {
   if (count < 0 || count > kMaxBatch) return -2;
   if (nstreams < 1 || nstreams > 64) return -7;
-  p->ns = nstreams < count ? nstreams : (count > 0 ? count : 1);
+  if (o->batch_small < 0) return -4;
+  const int small = small_limit(o);
   int order[kMaxBatch];
   for (int i = 0; i < count; ++i) order[i] = i;
   for (int a = 1; a < count; ++a) {  // stable insertion sort, M descending
@@ -821,11 +844,20 @@ int make_plan(int count, const int* M, const gep_options* o, const int* prec, in
     while (b >= 0 && M[order[b]] < M[t]) { order[b + 1] = order[b]; --b; }
     order[b + 1] = t;
   }
+  p->nsmall = 0;
+  for (int a = 0; a < count; ++a)
+    if (M[order[a]] >= 1 && M[order[a]] <= small) p->small_order[p->nsmall++] = order[a];
+  const int nbig = count - p->nsmall;
+  p->ns = nstreams < nbig ? nstreams : (nbig > 0 ? nbig : 1);
   double load[64] = {};
   for (int s = 0; s < 64; ++s) p->need[s] = 0;
   for (int a = 0; a < count; ++a) {
     int i = order[a];
     if (M[i] < 0) return -3;
+    if (M[i] >= 1 && M[i] <= small) {
+      p->assign[i] = -1;
+      continue;
+    }
     int best = 0;
     for (int s = 1; s < p->ns; ++s)
       if (load[s] < load[best]) best = s;
@@ -841,6 +873,9 @@ int make_plan(int count, const int* M, const gep_options* o, const int* prec, in
     p->off[s] = off;
     off += r256(p->need[s]);
   }
+  p->small_off = off;
+  p->small_ctas = p->nsmall < 2 * h->sm_count ? p->nsmall : 2 * h->sm_count;
+  off += p->nsmall ? r256(small_gep_scratch_bytes(p->small_ctas)) : 0;
   p->total = off;
   return GEP_OK;
 }
@@ -854,7 +889,7 @@ int gep_solve_batched_workspace_size(gep_handle_t h, int count, const int* M, co
   if (!o) return -4;
   if (!bytes) return -7;
   static BatchPlan plan;
-  GEP_CHECK(make_plan(count, M, o, precision, nstreams, &plan));
+  GEP_CHECK(make_plan(h, count, M, o, precision, nstreams, &plan));
   *bytes = plan.total;
   return GEP_OK;
 }
@@ -874,11 +909,12 @@ int gep_solve_batched(gep_handle_t h, int count, const int* M, double* const* A,
   }
   if (count == 0) return GEP_OK;
   static BatchPlan plan;
-  GEP_CHECK(make_plan(count, M, o, precision, nstreams, &plan));
+  GEP_CHECK(make_plan(h, count, M, o, precision, nstreams, &plan));
   if (h->ws == nullptr || h->ws_bytes < plan.total) return GEP_ERR_ALLOC;
   // child handles, streams and events are created once (outside any stream capture)
   if (!h->fork_ev) GEP_CUDA(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
   if (!h->d_batch_info) GEP_CUDA(cudaMalloc((void**)&h->d_batch_info, sizeof(int) * 2 * kMaxBatch));
+  if (!h->d_small_next) GEP_CUDA(cudaMalloc((void**)&h->d_small_next, 256));
   while (h->nchild < plan.ns) {
     int c = h->nchild;
     GEP_CUDA(cudaStreamCreateWithFlags(&h->child_stream[c], cudaStreamNonBlocking));
@@ -888,8 +924,13 @@ int gep_solve_batched(gep_handle_t h, int count, const int* M, double* const* A,
   }
   GEP_CUDA(cudaEventRecord(h->fork_ev, h->stream));
   for (int s = 0; s < plan.ns; ++s) GEP_CUDA(cudaStreamWaitEvent(h->child_stream[s], h->fork_ev, 0));
+  if (plan.nsmall > 0)  // the small pencils, on the handle's stream while the children run
+    GEP_CHECK(small_gep_batched(h, h->stream, plan.nsmall, M, A, B, w, Y, plan.small_order,
+                                (double*)(h->ws + plan.small_off), plan.small_ctas, h->d_small_next,
+                                h->d_batch_info));
   for (int i = 0; i < count; ++i) {
     int s = plan.assign[i];
+    if (s < 0) continue;
     gep_handle_t c = h->child[s];
     c->ws = h->ws + plan.off[s];
     c->ws_bytes = plan.need[s];

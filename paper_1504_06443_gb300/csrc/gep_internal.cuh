@@ -50,6 +50,7 @@ struct gep_handle_s {
   cudaEvent_t child_done[64] = {};
   cudaEvent_t fork_ev = nullptr;
   int* d_batch_info = nullptr;  // 2 ints per pencil of the last batched call
+  int* d_small_next = nullptr;  // work-queue counter of the one-CTA small-pencil launch
   int batch_count = 0;
   int refine_steps = 0;  // FP64 refinement steps taken by the last mixed-precision solve
 };
@@ -189,6 +190,18 @@ int refine_eigenpairs(gep_handle_t h, int M, const double* Af, const double* Bf,
 size_t adjoint_ws_elems(int M, int no);
 int adjoint(gep_handle_t h, int M, int no, const double* w, const double* Y, int ldy, const double* lbar,
             const double* W, int ldw, double* Abar, double* Bbar, int ldab, double* ws, int engine);
+
+// block-Jacobi SEP solver (jacobi.cu)
+size_t jacobi_ws_elems(int M);
+int jacobi_sep(gep_handle_t h, int M, double* C, int ldc, double* w, double* Z, int ldz, double* ws);
+
+// small pencils of a batched solve, one CTA each in one persistent launch (batched.cu)
+constexpr int SMALL_MAX = 128;         // largest order solved by one CTA
+constexpr int SMALL_PER_LAUNCH = 256;  // pencils whose table one launch carries in its parameters
+size_t small_gep_scratch_bytes(int ctas);
+int small_gep_batched(gep_handle_t h, cudaStream_t s, int count, const int* M, double* const* A, double* const* B,
+                      double* const* w, double* const* Y, const int* order, double* scratch, int ctas, int* next,
+                      int* info);
 
 // Kernel-side helper: returns true when an earlier stage recorded an error.
 __device__ __forceinline__ bool status_bad(const int* st) { return st != nullptr && (st[0] != 0 || st[1] != 0); }

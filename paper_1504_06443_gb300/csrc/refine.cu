@@ -20,6 +20,7 @@
 #include <math.h>
 
 #include "gep_internal.cuh"
+#include "cta_eig.cuh"
 
 namespace gep {
 namespace {
@@ -301,9 +302,7 @@ __global__ void k_cluster_solve(int M, const double* __restrict__ S, const doubl
 }
 
 // One CTA per cluster of KMAX < k <= KBIG members (a chain of near-degenerate eigenvalues):
-// the exact solve of k_cluster_solve with its steps spread over the CTA.  The triangular
-// solves take one column (row) per thread; cyclic Jacobi runs in round-robin order, whose
-// k/2 rotations of a round touch disjoint index pairs and are applied together.
+// the exact solve of k_cluster_solve with its steps spread over the CTA (cta_pencil_eig).
 __global__ void __launch_bounds__(256) k_cluster_solve_big(int M, const double* __restrict__ S,
                                                            const double* __restrict__ R,
                                                            const int* __restrict__ cstart,
@@ -311,9 +310,7 @@ __global__ void __launch_bounds__(256) k_cluster_solve_big(int M, const double* 
                                                            const long long* __restrict__ coff, const int* ncl,
                                                            double* __restrict__ lam, double* __restrict__ E,
                                                            double* __restrict__ scratch, const int* st) {
-  __shared__ double csv[KBIG / 2], snv[KBIG / 2], red[8];
-  __shared__ int pa[KBIG / 2], pb[KBIG / 2], pos[KBIG];
-  __shared__ int done;
+  __shared__ CtaEigShared sh;
   if (status_bad(st)) return;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int c = blockIdx.x; c < ncl[0]; c += gridDim.x) {
@@ -327,159 +324,10 @@ __global__ void __launch_bounds__(256) k_cluster_solve_big(int M, const double* 
       int a = max(s0 + p, s0 + q), b = min(s0 + p, s0 + q);
       L[idx] = R[GEP_IX(a, b, M)];
       Cm[idx] = S[GEP_IX(a, b, M)];
-      V[idx] = (p == q) ? 1.0 : 0.0;
     }
     __syncthreads();
-    // Cholesky R_CC = L L^T (right-looking, lower triangle)
-    for (int j = 0; j < k; ++j) {
-      if (tid == 0) L[j + j * k] = sqrt(fmax(L[j + j * k], 1e-300));
-      __syncthreads();
-      const double d = L[j + j * k];
-      for (int i = j + 1 + tid; i < k; i += nt) L[i + j * k] /= d;
-      __syncthreads();
-      const int w = k - j - 1;
-      for (int t = tid; t < w * w; t += nt) {
-        int i = j + 1 + t % w, q = j + 1 + t / w;
-        if (i >= q) L[i + q * k] -= L[i + j * k] * L[q + j * k];
-      }
-      __syncthreads();
-    }
-    // Cm <- L^-1 Cm (each column a forward substitution), then Cm <- Cm L^-T (each row)
-    for (int q = tid; q < k; q += nt)
-      for (int i = 0; i < k; ++i) {
-        double t = Cm[i + q * k];
-        for (int p = 0; p < i; ++p) t -= L[i + p * k] * Cm[p + q * k];
-        Cm[i + q * k] = t / L[i + i * k];
-      }
-    __syncthreads();
-    for (int i = tid; i < k; i += nt)
-      for (int q = 0; q < k; ++q) {
-        double t = Cm[i + q * k];
-        for (int p = 0; p < q; ++p) t -= Cm[i + p * k] * L[q + p * k];
-        Cm[i + q * k] = t / L[q + q * k];
-      }
-    __syncthreads();
-    // parallel cyclic Jacobi: n = k rounded up to even (index k, if present, is a dummy)
-    const int n = (k + 1) & ~1, half = n / 2;
-    for (int i = tid; i < n; i += nt) pos[i] = i;
-    if (tid == 0) done = 0;
-    __syncthreads();
-    for (int sweep = 0; sweep < 30 && !done; ++sweep) {
-      double off = 0.0, tot = 0.0;
-      for (int idx = tid; idx < k * k; idx += nt) {
-        double x = Cm[idx];
-        tot += x * x;
-        if (idx % k != idx / k) off += x * x;
-      }
-      for (int o = 16; o; o >>= 1) {
-        off += __shfl_xor_sync(0xffffffffu, off, o);
-        tot += __shfl_xor_sync(0xffffffffu, tot, o);
-      }
-      if ((tid & 31) == 0) { red[tid >> 5] = off; }
-      __syncthreads();
-      if (tid == 0) {
-        double so = 0.0;
-        for (int w = 0; w < nt / 32; ++w) so += red[w];
-        red[0] = so;
-      }
-      __syncthreads();
-      const double offs = red[0];
-      __syncthreads();
-      if ((tid & 31) == 0) red[tid >> 5] = tot;
-      __syncthreads();
-      if (tid == 0) {
-        double st2 = 0.0;
-        for (int w = 0; w < nt / 32; ++w) st2 += red[w];
-        done = offs <= 1e-28 * st2;  // off-diagonal entries ~1e-14 of the matrix: FP64 level
-      }
-      __syncthreads();
-      if (done) break;
-      for (int round = 0; round < n - 1; ++round) {
-        for (int t = tid; t < half; t += nt) {
-          int a = pos[t], b = pos[n - 1 - t];
-          int p = min(a, b), q = max(a, b);
-          double cs = 1.0, sn = 0.0;
-          if (q < k) {
-            double apq = 0.5 * (Cm[p + q * k] + Cm[q + p * k]);
-            if (apq != 0.0) {
-              double th = (Cm[q + q * k] - Cm[p + p * k]) / (2.0 * apq);
-              double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-              cs = 1.0 / sqrt(tt * tt + 1.0);
-              sn = tt * cs;
-            }
-          }
-          pa[t] = p;
-          pb[t] = q;
-          csv[t] = cs;
-          snv[t] = sn;
-        }
-        __syncthreads();
-        // columns of Cm and V
-        for (int idx = tid; idx < half * k; idx += nt) {
-          int t = idx / k, r = idx % k;
-          if (pb[t] >= k || snv[t] == 0.0) continue;
-          int p = pa[t], q = pb[t];
-          double cs = csv[t], sn = snv[t];
-          double x = Cm[r + p * k], y = Cm[r + q * k];
-          Cm[r + p * k] = cs * x - sn * y;
-          Cm[r + q * k] = sn * x + cs * y;
-          x = V[r + p * k];
-          y = V[r + q * k];
-          V[r + p * k] = cs * x - sn * y;
-          V[r + q * k] = sn * x + cs * y;
-        }
-        __syncthreads();
-        // rows of Cm
-        for (int idx = tid; idx < half * k; idx += nt) {
-          int t = idx / k, r = idx % k;
-          if (pb[t] >= k || snv[t] == 0.0) continue;
-          int p = pa[t], q = pb[t];
-          double cs = csv[t], sn = snv[t];
-          double x = Cm[p + r * k], y = Cm[q + r * k];
-          Cm[p + r * k] = cs * x - sn * y;
-          Cm[q + r * k] = sn * x + cs * y;
-        }
-        __syncthreads();
-        if (tid == 0) {  // round-robin: position 0 stays, the others rotate by one
-          int last = pos[n - 1];
-          for (int i = n - 1; i > 1; --i) pos[i] = pos[i - 1];
-          pos[1] = last;
-        }
-        __syncthreads();
-      }
-    }
-    __syncthreads();
-    // ascending order of the cluster's eigenvalues (selection sort; column swaps in parallel)
-    for (int a = 0; a < k; ++a) {
-      if (tid == 0) {
-        int m = a;
-        for (int b = a + 1; b < k; ++b)
-          if (Cm[b + b * k] < Cm[m + m * k]) m = b;
-        pos[0] = m;
-      }
-      __syncthreads();
-      const int m = pos[0];
-      if (m != a) {
-        for (int r = tid; r < k; r += nt) {
-          double x = V[r + a * k];
-          V[r + a * k] = V[r + m * k];
-          V[r + m * k] = x;
-        }
-        if (tid == 0) {
-          double t = Cm[a + a * k];
-          Cm[a + a * k] = Cm[m + m * k];
-          Cm[m + m * k] = t;
-        }
-      }
-      __syncthreads();
-    }
-    // W = L^-T V (each column a back substitution), E_CC = W - I
+    cta_pencil_eig(k, L, Cm, V, sh, false);  // R_CC: Gram matrix of nearly B-orthonormal vectors
     for (int q = tid; q < k; q += nt) {
-      for (int i = k - 1; i >= 0; --i) {
-        double t = V[i + q * k];
-        for (int p = i + 1; p < k; ++p) t -= L[p + i * k] * V[p + q * k];
-        V[i + q * k] = t / L[i + i * k];
-      }
       for (int p = 0; p < k; ++p) E[GEP_IX(s0 + p, s0 + q, M)] = V[p + q * k] - (p == q ? 1.0 : 0.0);
       lam[s0 + q] = Cm[q + q * k];
     }

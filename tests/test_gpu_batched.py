@@ -130,3 +130,61 @@ def test_batched_workload_shapes_vs_oracle(gep, batch_vs_oracle, precision):
     torch.cuda.synchronize()
     assert bs.info() == 0
     _check_against_oracle(bs.results(), pencils, "graph")
+
+
+def test_batched_small_pencils_one_cta_vs_oracle(gep, oracle_lib):
+    """Pencils of order <= 128 solved whole by one CTA each in one persistent launch (the
+    rest of the batch on the streams), eager and replayed from a captured graph, against the
+    oracle at the FP64 tolerances."""
+    import torch
+    orders = [64, 72, 128, 100, 96, 256, 68, 120, 88, 340, 64, 112]
+    pencils = []
+    for i, M in enumerate(orders):
+        tb = gi.tight_binding(M, seed=7000 + i)
+        w_ref, Y_ref, info = oracle_lib.gep_solve(tb["A"], tb["B"])
+        assert info == 0
+        pencils.append(dict(A=tb["A"], B=tb["B"], w=w_ref, Y=Y_ref, nA=_two_norm(tb["A"])))
+    As = [dev(p["A"]) for p in pencils]
+    Bs = [dev(p["B"]) for p in pencils]
+    bs = gep.BatchedSolver(As, Bs, nstreams=4, precision="fp64_emulated", batch_small=128)
+    bs.run()
+    torch.cuda.synchronize()
+    assert bs.info() == 0
+    _check_against_oracle(bs.results(), pencils, "eager")
+    bs.capture()
+    for w, Yt in zip(bs.w, bs.Yt):
+        w.zero_()
+        Yt.zero_()
+    bs.replay()
+    torch.cuda.synchronize()
+    assert bs.info() == 0
+    _check_against_oracle(bs.results(), pencils, "graph")
+
+
+def test_batched_small_pencil_status(gep):
+    """A small pencil whose B is not positive definite reports its first bad leading minor
+    through the batched status, like the staged workflow; a NaN reports GEP_ERR_NONFINITE."""
+    import torch
+    good = gi.tight_binding(64, seed=1)
+    Bbad = np.array(good["B"])
+    Bbad[10, 10] = -1.0
+    As = [dev(good["A"]), dev(good["A"])]
+    Bs = [dev(good["B"]), dev(Bbad)]
+    bs = gep.BatchedSolver(As, Bs, nstreams=1, batch_small=128)
+    bs.run()
+    torch.cuda.synchronize()
+    assert bs.info() > 0
+    An = np.array(good["A"])
+    An[5, 3] = np.nan
+    bs2 = gep.BatchedSolver([dev(good["A"]), dev(An)], [dev(good["B"]), dev(good["B"])], nstreams=1, batch_small=128)
+    bs2.run()
+    torch.cuda.synchronize()
+    assert bs2.info() == gep.ERR_NONFINITE
+
+
+def test_autotuner_small_choice(gep):
+    orders = [64, 80, 96, 128]
+    As, Bs = _batch(3100, orders)
+    tuner = gep.Autotuner()
+    tuner.tune(As[:1], Bs[:1], reps=1)
+    assert tuner.tune_small(As, Bs) in (0, 128)
