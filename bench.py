@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--batched", action="store_true",
                    help="512 tight-binding pencils, orders log-uniform in [64, 2048], one captured graph")
     p.add_argument("--batch-count", type=int, default=512)
+    p.add_argument("--batch-small", type=int, default=-1,
+                   help="--batched: order limit of the one-CTA route (-1: autotuned, 0: off, <= 128)")
     p.add_argument("--adjoint", action="store_true",
                    help="forward+adjoint of sum(lambda_occ) + <W, P> at M=4096 with central differences")
     p.add_argument("--fd-dirs", type=int, default=64)
@@ -164,7 +166,7 @@ def run_batched(a):
     reps = [next(i for i, M in enumerate(orders) if gep._bucket(M) == b) for b in sorted({gep._bucket(M) for M in orders})]
     tuner = gep.Autotuner()
     choice = tuner.tune([As[i] for i in reps], [Bs[i] for i in reps], reps=1)
-    small = tuner.tune_small(As, Bs)
+    small = tuner.tune_small(As, Bs) if a.batch_small < 0 else a.batch_small
     precs = [tuner.precision_for(M) for M in orders]
     flops = sum(7.0 * float(M) ** 3 for M in orders)
     # looping single solves on one stream (baseline)

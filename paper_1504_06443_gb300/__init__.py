@@ -714,19 +714,19 @@ class Autotuner:
         self.batch_small = 0
 
     def tune_small(self, As, Bs, nstreams=16, reps=1):
-        """Times the pencils of order <= 128 both ways (one-CTA persistent launch, staged
-        workflow with the tuned engines) and keeps the faster: sets self.batch_small."""
+        """Times the whole batch both ways (pencils of order <= 128 in one persistent launch of
+        one CTA each, or all of them on the streams, with the tuned engines) and keeps the
+        faster: sets self.batch_small.  The whole batch is timed because the two routes share
+        the GPU with the larger pencils."""
         import time
         torch = _torch()
-        pick = [i for i, a in enumerate(As) if int(a.shape[0]) <= 128]
-        if not pick:
+        if not any(int(a.shape[0]) <= 128 for a in As):
             self.batch_small = 0
             return self.batch_small
-        sa, sb = [As[i] for i in pick], [Bs[i] for i in pick]
         best, best_t = 0, None
         for small in (128, 0):
-            bs = BatchedSolver(sa, sb, nstreams=nstreams, batch_small=small,
-                               precisions=[self.precision_for(int(a.shape[0])) for a in sa])
+            bs = BatchedSolver(As, Bs, nstreams=nstreams, batch_small=small,
+                               precisions=[self.precision_for(int(a.shape[0])) for a in As])
             bs.run()
             torch.cuda.synchronize()
             t0 = time.perf_counter()

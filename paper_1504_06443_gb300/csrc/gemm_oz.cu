@@ -76,78 +76,64 @@ __global__ void k_rowexp_slab(int R, int K, const double* __restrict__ X, long l
   if (m) atomicMax(raw + r, m);
 }
 
-// Exact BF16 bit pattern of a small integer d (|d| <= 256): 1.5 * 2^23 + d is a float of
-// the binade [2^23, 2^24) whose last bits are d, so subtracting 1.5 * 2^23 gives d exactly
-// as an FP32 value, and with at most 9 significant bits its upper half is its BF16 pattern.
-__device__ __forceinline__ unsigned bf16_of_int(int d) {
-  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
-  return (unsigned)__float_as_int(f) >> 16;
-}
-
-// Balanced base-128 digits of the fixed-point integer F (|F| < 2^(7S)), least significant
-// first: d_S..d_2 in [-64, 63], the leading d_1 what remains.  32-bit integer arithmetic
-// only: for S > 4 the low 28 bits give four digits and their carry joins the upper part.
-template <int S>
-__device__ __forceinline__ void digits_of(long long F, int* d) {
-  int v;
-  int q = S - 1;  // index of the next digit to produce (d[0] = d_1)
-  if (S > 4) {
-    int lo = (int)(F & 0x0FFFFFFFll);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      int x = lo & 127;
-      x -= (x >= 64) ? 128 : 0;
-      lo = (lo - x) >> 7;
-      d[q--] = x;
-    }
-    v = (int)(F >> 28) + lo;
-  } else {
-    v = (int)F;
-  }
-#pragma unroll
-  for (int u = 0; u < (S > 4 ? S - 5 : S - 1); ++u) {
-    int x = v & 127;
-    x -= (x >= 64) ? 128 : 0;
-    v = (v - x) >> 7;
-    d[q--] = x;
-  }
-  d[0] = v;
-}
-
-// F = round(x 2^(7S - e)) as a signed integer (|F| < 2^(7S)), from the IEEE bits.
+// F = round(x 2^(7S - e)) as a signed integer (|F| < 2^(7S)), from the IEEE bits: the
+// magnitude is rounded half away from zero (error at most half a unit of the last digit).
+// The row's own exponent e keeps the left shift at most 3.
 __device__ __forceinline__ long long to_fixed(double x, int e, int S) {
-  long long bits = __double_as_longlong(x);
-  int E = (int)((bits >> 52) & 0x7FF);
+  const long long bits = __double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7FF);
   if (E == 0) return 0;
-  unsigned long long m = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  int sh = E - 1075 + 7 * S - e;
+  const unsigned long long m = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = E - 1075 + 7 * S - e;
   unsigned long long qv;
-  if (sh >= 0) {
-    qv = m << sh;
-  } else if (sh > -64) {
-    int rs = -sh;
-    qv = m >> rs;
-    unsigned long long rem = m & ((1ull << rs) - 1ull), half = 1ull << (rs - 1);
-    if (rem > half || (rem == half && (qv & 1ull))) ++qv;
-  } else {
-    qv = 0;
-  }
+  if (sh >= 0) qv = m << sh;
+  else if (sh > -54) qv = (m + (1ull << (-sh - 1))) >> (-sh);
+  else qv = 0;  // below half a unit of the last digit
   return (bits < 0) ? -(long long)qv : (long long)qv;
 }
 
+// 64 in every digit position below the leading one: F + this has base-128 digits
+// d_s + 64 in [0, 127] for s >= 2 (d_s in [-64, 63]) and d_1 above them.
+template <int S>
+__device__ __forceinline__ constexpr long long digit_offset() {
+  long long o = 0;
+  for (int i = 0; i < S - 1; ++i) o = o * 128 + 64;
+  return o;
+}
+
+// FP32 bit pattern of the small integer d + bias (|d + bias| <= 256): 1.5 * 2^23 + d is a
+// float of the binade [2^23, 2^24) whose last bits are d, and subtracting 1.5 * 2^23 leaves
+// d exactly; with at most 9 significant bits its upper half is its BF16 pattern.
+__device__ __forceinline__ unsigned f32_bits_of_int(int d, int bias) {
+  return (unsigned)__float_as_int(__int_as_float(0x4B400000 + bias + d) - 12582912.0f);
+}
+
+// Balanced base-128 digits of the fixed-point integer F (|F| < 2^(7S)): d_S..d_2 in
+// [-64, 63] and the leading d_1 (the same digits the peel "d = F mod 128 in [-64, 63],
+// F <- (F - d) / 128" gives, from the least significant end).  With the offset above they
+// are plain bit fields of F + offset, so no carries are propagated.  f[0] holds d_1.
+template <int S>
+__device__ __forceinline__ void digit_bits(long long F, unsigned* f) {
+  const long long Fp = F + digit_offset<S>();
+  f[0] = f32_bits_of_int((int)(Fp >> (7 * (S - 1))), 0);
+#pragma unroll
+  for (int s = 1; s < S; ++s) f[s] = f32_bits_of_int((int)((Fp >> (7 * (S - 1 - s))) & 127), -64);
+}
+
 // Digits of 4 consecutive elements x[0..3] of row r (columns kk .. kk+3, all < Kpad;
-// columns >= K are zero) written as one 8-byte store per plane.
+// columns >= K are zero) written as one 8-byte store per plane; the BF16 patterns (upper
+// halves of the FP32 patterns) are paired by byte permutes.
 template <int SC>
 __device__ __forceinline__ void split4_store_t(const double* x, int kk, int K, int e, size_t base, size_t plane,
                                                unsigned short* __restrict__ out) {
-  int d[4][SC];
+  unsigned f[4][SC];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) digits_of<SC>((kk + u < K) ? to_fixed(x[u], e, SC) : 0ll, d[u]);
+  for (int u = 0; u < 4; ++u) digit_bits<SC>((kk + u < K) ? to_fixed(x[u], e, SC) : 0ll, f[u]);
 #pragma unroll
   for (int s = 0; s < SC; ++s) {
     uint2 w;
-    w.x = bf16_of_int(d[0][s]) | (bf16_of_int(d[1][s]) << 16);
-    w.y = bf16_of_int(d[2][s]) | (bf16_of_int(d[3][s]) << 16);
+    w.x = __byte_perm(f[0][s], f[1][s], 0x7632);
+    w.y = __byte_perm(f[2][s], f[3][s], 0x7632);
     *reinterpret_cast<uint2*>(out + base + (size_t)s * plane) = w;
   }
 }

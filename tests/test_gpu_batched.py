@@ -175,7 +175,7 @@ def test_batched_small_pencil_status(gep):
     torch.cuda.synchronize()
     assert bs.info() > 0
     An = np.array(good["A"])
-    An[5, 3] = np.nan
+    An[5, 3] = An[3, 5] = np.nan
     bs2 = gep.BatchedSolver([dev(good["A"]), dev(An)], [dev(good["B"]), dev(good["B"])], nstreams=1, batch_small=128)
     bs2.run()
     torch.cuda.synchronize()
@@ -185,6 +185,7 @@ def test_batched_small_pencil_status(gep):
 def test_autotuner_small_choice(gep):
     orders = [64, 80, 96, 128]
     As, Bs = _batch(3100, orders)
+    As2, Bs2 = _batch(3200, [300, 520])
     tuner = gep.Autotuner()
-    tuner.tune(As[:1], Bs[:1], reps=1)
-    assert tuner.tune_small(As, Bs) in (0, 128)
+    tuner.tune(As[:1] + As2, Bs[:1] + Bs2, reps=1)
+    assert tuner.tune_small(As + As2, Bs + Bs2) in (0, 128)
