@@ -254,7 +254,7 @@ def run_adjoint(a):
     gap = float((w[n] - w[n - 1]).item())
     rng = np.random.default_rng(2)
     h = 1e-6
-    errs = []
+    errs, errs2, errs_r = [], [], []
     with torch.no_grad():
         for _ in range(a.fd_dirs):
             dA = rng.standard_normal((M, M)); dA = dA + dA.T
@@ -262,15 +262,23 @@ def run_adjoint(a):
             dA *= 1e-3 * np.linalg.norm(tb["A"]) / np.linalg.norm(dA)
             dB *= 0.1 * 0.1 / np.linalg.norm(dB)
             dAt, dBt = torch.as_tensor(dA).cuda(), torch.as_tensor(dB).cuda()
-            fp, _ = loss_of(A + h * dAt, B + h * dBt)
-            fm, _ = loss_of(A - h * dAt, B - h * dBt)
-            fd = (fp - fm).item() / (2 * h)
             an = float((gA * dAt).sum() + (gB * dBt).sum())
-            errs.append(abs(fd - an) / max(1.0, abs(fd)))
+            fd = {}
+            for hh in (h, 2 * h):  # central differences at h and 2h (Richardson: O(h^4))
+                fp, _ = loss_of(A + hh * dAt, B + hh * dBt)
+                fm, _ = loss_of(A - hh * dAt, B - hh * dBt)
+                fd[hh] = (fp - fm).item() / (2 * hh)
+            rich = (4.0 * fd[h] - fd[2 * h]) / 3.0
+            errs.append(abs(fd[h] - an) / max(1.0, abs(fd[h])))
+            errs2.append(abs(fd[2 * h] - an) / max(1.0, abs(fd[2 * h])))
+            errs_r.append(abs(rich - an) / max(1.0, abs(rich)))
     out = {"metric": "differentiable GEP: forward + adjoint time", "M": M, "n_occ": n, "unit": "s",
            "forward_s": e0.elapsed_time(e1) / 1e3, "backward_s": e1.elapsed_time(e2) / 1e3,
            "value": e0.elapsed_time(e2) / 1e3, "higher_is_better": False, "homo_lumo_gap": gap,
            "fd_directions": a.fd_dirs, "fd_h": h, "fd_max_rel_err": max(errs) if errs else None,
+           "fd_median_rel_err": float(np.median(errs)) if errs else None,
+           "fd_2h_max_rel_err": max(errs2) if errs2 else None,
+           "fd_richardson_max_rel_err": max(errs_r) if errs_r else None,
            "data": "synthetic", "dtype": "f64",
            "config": {"workload": f"tight-binding GEP M={M}, loss = sum_occ lambda + <W, Y_o Y_o^T>"}}
     print(json.dumps(out), flush=True)

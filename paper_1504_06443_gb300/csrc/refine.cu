@@ -96,7 +96,8 @@ __global__ void k_pair_far(int M, const double* __restrict__ S, const double* __
 // thread): cstart/csize/coff (scratch offset) per cluster, ncl[0] = number of clusters,
 // cid[i] = the cluster of index i when that cluster is solved exactly (k <= KBIG),
 // -2 - c when i lies in cluster c of more than KBIG members (chained near-degenerate
-// eigenvalues; its inner pairs only get their B-orthogonality restored), else -1.
+// eigenvalues; its inner pairs take the first-order step where their own gap is safe and
+// only get their B-orthogonality restored otherwise), else -1.
 // Scratch use is sum 3 k^2 <= 3 M min(M, KBIG).
 __global__ void k_clusters(int M, const int* __restrict__ far, int* cstart, int* csize, long long* coff, int* cid,
                            int* ncl, const int* st) {
@@ -148,10 +149,18 @@ __global__ void k_refine_E(int M, const double* __restrict__ S, const double* __
       e = 0.0;
       m = fmax(m, fabs(rij));
     } else if (cid[i] <= -2 && cid[i] == cid[j]) {
-      // inside a cluster too large to solve exactly the first-order step may be large
-      // (gap below the error level): restore B-orthogonality only
-      e = -0.5 * rij;
-      m = fmax(m, fabs(rij));
+      // inside a cluster too large to solve exactly (a chain formed through the global
+      // threshold): the first-order step where the pair's own gap allows it, else restore
+      // B-orthogonality only
+      const double gap = lam[j] - lam[i], sij = S[GEP_IX(a, b, M)];
+      const double res = fmax(fabs(sij - lam[j] * rij), fabs(sij - lam[i] * rij));
+      if (fabs(gap) > fmax(THETA * res, delta)) {
+        e = (sij - lam[j] * rij) / gap;
+        m = fmax(m, fabs(e));
+      } else {
+        e = -0.5 * rij;
+        m = fmax(m, fabs(rij));
+      }
     } else {
       double gap = lam[j] - lam[i];
       if (fabs(gap) <= delta) e = -0.5 * rij;
