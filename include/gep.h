@@ -232,6 +232,18 @@ int gep_solve_batched_workspace_size(gep_handle_t h, int count, const int* M, co
                                      const int* precision, int nstreams, size_t* bytes);
 int gep_solve_batched(gep_handle_t h, int count, const int* M, double* const* A, double* const* B, double* const* w,
                       double* const* Y, const gep_options* o, const int* precision, int nstreams);
+/* As gep_solve_batched / gep_solve_batched_workspace_size, with one gep_options per pencil
+ * (opts[0..count), host memory): pencil i runs its own workflow (reducer, SEP solver,
+ * bandwidth, precision, want_vectors; the autotuned route of its size bucket) and takes the
+ * one-CTA route when M[i] <= opts[i].batch_small.  timers are ignored and n_want must be 0.
+ * Returns -2 (count outside 0..4096), -3 (a null array or a negative order), -4 (opts null
+ * or a negative batch_small; -8 in gep_solve_batched_opts), -5 / -9 (nstreams outside
+ * 1..64), -6 (bytes null), GEP_ERR_UNSUPPORTED for an unsupported option set,
+ * GEP_ERR_ALLOC for a workspace smaller than the query's answer. */
+int gep_solve_batched_opts_workspace_size(gep_handle_t h, int count, const int* M, const gep_options* opts,
+                                          int nstreams, size_t* bytes);
+int gep_solve_batched_opts(gep_handle_t h, int count, const int* M, double* const* A, double* const* B,
+                           double* const* w, double* const* Y, const gep_options* opts, int nstreams);
 /* Synchronises and returns max over child streams of their numerical status. */
 int gep_batched_info(gep_handle_t h, int* info);
 
@@ -281,7 +293,8 @@ int gep_refine_steps(gep_handle_t h);
  * Synchronises with that solve; GEP_ERR_UNSUPPORTED when none was recorded. */
 int gep_get_band_times(gep_handle_t h, double t[2]);
 
-/* Number of kernels the library launched since gep_create / last reset. */
+/* Number of kernels the library launched since gep_create / last reset (for
+ * gep_solve_batched: every kernel of the batch, the child streams' included). */
 long long gep_launch_count(gep_handle_t h, int reset);
 
 /* Per-launch timing of the split-BF16 tensor-core product kernel (measurement aid;

@@ -111,6 +111,9 @@ def load():
             "gep_solve_batched_workspace_size": (_I, [_P, _I, _P, ctypes.POINTER(GepOptions), _P, _I,
                                                      ctypes.POINTER(_SZ)]),
             "gep_solve_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(GepOptions), _P, _I]),
+            "gep_solve_batched_opts_workspace_size": (_I, [_P, _I, _P, ctypes.POINTER(GepOptions), _I,
+                                                          ctypes.POINTER(_SZ)]),
+            "gep_solve_batched_opts": (_I, [_P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(GepOptions), _I]),
             "gep_batched_info": (_I, [_P, ctypes.POINTER(_I)]),
             "gep_dgemm": (_I, [_P, ctypes.c_char, ctypes.c_char, ctypes.c_char, _I, _I, _I, _D, _P, _I, _P, _I,
                                _D, _P, _I, _I]),
@@ -385,9 +388,12 @@ def solve_async(A, B, w, Yt, opts, handle):
     """Enqueue-only variant used by the benchmark: no synchronisation, no allocation."""
     _need_matrix(A, "A", square=True, f64=True, cuda=False)
     _need_matrix(B, "B", rows=A.shape[0], cols=A.shape[0], f64=True, cuda=False)
-    _need_vector(w, "w", A.shape[0], f64=True, cuda=False)
+    n = int(opts.n_want) if opts.n_want else int(A.shape[0])  # w: n entries, Yt: n x M (Y^T)
+    _need_vector(w, "w", n, f64=True, cuda=False)
     if Yt is not None:
-        _need_matrix(Yt, "Yt", rows=A.shape[0], cols=A.shape[0], f64=True, cuda=False)
+        _need_matrix(Yt, "Yt", rows=n, cols=A.shape[0], f64=True, cuda=False)
+        if not Yt.is_contiguous():
+            raise ValueError("Yt must be contiguous")
     _need_on_device("A", A, "B", B, "w", w, "Yt", Yt)
     pa, lda = _sym_ptr_ld(A)
     pb, ldb = _sym_ptr_ld(B)
@@ -704,20 +710,23 @@ def _bucket(M):
 
 
 class Autotuner:
-    """Per size bucket, the faster of the two FP64-accurate product engines (FP64 FMA
-    tiles or split-BF16 tensor-core tiles), timed on one pencil of the bucket; and, for the
-    pencils of order <= 128, whether solving each whole in one CTA of one persistent launch
-    (batch_small) beats the staged workflow on concurrent streams, timed on those pencils."""
+    """Per size bucket, the fastest route of one pencil of the bucket: the FP64-accurate
+    product engine (FP64 FMA tiles or split-BF16 tensor-core tiles) and the SEP reduction
+    (1-stage tridiagonalisation or full -> band -> tridiagonal); and, for the pencils of
+    order <= 128, whether solving each whole in one CTA of one persistent launch
+    (batch_small) beats the staged workflow on concurrent streams, timed on the batch."""
 
     def __init__(self):
-        self.choice = {}
+        self.choice = {}      # bucket -> engine
+        self.sep_choice = {}  # bucket -> SEP reduction
         self.batch_small = 0
 
-    def tune_small(self, As, Bs, nstreams=16, reps=1):
+    def tune_small(self, As, Bs, nstreams=16, reps=1, precision=None):
         """Times the whole batch both ways (pencils of order <= 128 in one persistent launch of
-        one CTA each, or all of them on the streams, with the tuned engines) and keeps the
-        faster: sets self.batch_small.  The whole batch is timed because the two routes share
-        the GPU with the larger pencils."""
+        one CTA each, or all of them on the streams, with the tuned routes, or with
+        `precision` for every pencil when given) and keeps the faster: sets self.batch_small.
+        The whole batch is timed because the two routes share the GPU with the larger
+        pencils."""
         import time
         torch = _torch()
         if not any(int(a.shape[0]) <= 128 for a in As):
@@ -726,7 +735,8 @@ class Autotuner:
         best, best_t = 0, None
         for small in (128, 0):
             bs = BatchedSolver(As, Bs, nstreams=nstreams, batch_small=small,
-                               precisions=[self.precision_for(int(a.shape[0])) for a in As])
+                               precisions=[precision or self.precision_for(int(a.shape[0])) for a in As],
+                               seps=[self.sep_for(int(a.shape[0])) for a in As])
             bs.run()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -736,10 +746,14 @@ class Autotuner:
             t = (time.perf_counter() - t0) / reps
             if best_t is None or t < best_t:
                 best, best_t = small, t
+            bs.close()
         self.batch_small = best
         return best
 
-    def tune(self, As, Bs, reps=2):
+    def tune(self, As, Bs, reps=2, seps=("1stage",), engines=("fp64", "fp64_emulated")):
+        """Times every engine x SEP reduction (from `engines`, `seps`) on the first pencil of
+        each size bucket and keeps the fastest; returns the engine per bucket (sep_for gives
+        the reduction)."""
         import time
         torch = _torch()
         for A, B in zip(As, Bs):
@@ -747,31 +761,81 @@ class Autotuner:
             if b in self.choice:
                 continue
             best, best_t = None, None
-            for eng in ("fp64", "fp64_emulated"):
-                solve(A, B, precision=eng)
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                for _ in range(reps):
-                    solve(A, B, precision=eng)
-                torch.cuda.synchronize()
-                t = (time.perf_counter() - t0) / reps
-                if best_t is None or t < best_t:
-                    best, best_t = eng, t
-            self.choice[b] = best
+            for sep in seps:
+                for eng in engines:
+                    solve(A, B, precision=eng, sep=sep)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    for _ in range(reps):
+                        solve(A, B, precision=eng, sep=sep)
+                    torch.cuda.synchronize()
+                    t = (time.perf_counter() - t0) / reps
+                    if best_t is None or t < best_t:
+                        best, best_t = (eng, sep), t
+            self.choice[b], self.sep_choice[b] = best
         return self.choice
+
+    def tune_routes(self, As, Bs, nstreams=16, thresholds=(None, 1024, 512, 0), precision=None):
+        """Chooses, for the whole batch, the order above which pencils take the 2-stage route
+        (None: none do): every candidate is captured into a graph and one replay is timed
+        after a warm-up replay.  The 1-stage route launches six kernels per column, so its
+        graphs are large; a candidate whose batch launches more kernels than one graph may
+        hold (BatchedSolver.GRAPH_KERNEL_LIMIT) is skipped.  Sets sep_choice per bucket and
+        returns the chosen threshold."""
+        torch = _torch()
+        best, best_t = None, None
+        for T in thresholds:
+            seps = ["2stage" if (T is not None and int(a.shape[0]) > T) else "1stage" for a in As]
+            bs = BatchedSolver(As, Bs, nstreams=nstreams, batch_small=self.batch_small, seps=seps,
+                               precisions=[precision or self.precision_for(int(a.shape[0])) for a in As])
+            try:
+                bs.capture()
+            except ValueError:
+                bs.close()
+                continue
+            bs.replay()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            bs.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            bs.close()
+            if best_t is None or t < best_t:
+                best, best_t = T, t
+        self.sep_threshold = best
+        for b in SIZE_BUCKETS:
+            self.sep_choice[b] = "2stage" if (best is not None and b > best) else "1stage"
+        return best
 
     def precision_for(self, M):
         return self.choice.get(_bucket(M), "fp64_emulated")
 
+    def sep_for(self, M):
+        if getattr(self, "sep_threshold", "unset") != "unset":
+            T = self.sep_threshold
+            return "2stage" if (T is not None and M > T) else "1stage"
+        return self.sep_choice.get(_bucket(M), "1stage")
+
 
 class BatchedSolver:
-    """Many independent pencils (A_i, B_i) solved by gep_solve_batched over `nstreams`
-    concurrent streams; capture() records the whole batch into one CUDA graph that
+    """Many independent pencils (A_i, B_i) solved by gep_solve_batched_opts over `nstreams`
+    concurrent streams, each pencil with its own route (precisions / seps per pencil, else
+    precision / sep for all); capture() records the whole batch into one CUDA graph that
     replay() launches again (inputs are read from the same device buffers each time).
-    batch_small > 0: pencils of order <= batch_small (at most 128) are solved whole by one
-    CTA each, all in one persistent launch."""
+    batch_small > 0 (default 128): pencils of order <= batch_small (at most 128) are solved
+    whole by one CTA each, all in one persistent launch; 0 puts every pencil on the streams.
 
-    def __init__(self, As, Bs, nstreams=8, precision="fp64_emulated", precisions=None, handle=None, batch_small=0):
+    capture() refuses a batch whose eager run launched more than GRAPH_KERNEL_LIMIT kernels:
+    graphs of about two million kernel nodes or more ended in a host crash inside the graph
+    launch on this GPU's driver, with a GPU fault reported for the process.  Split such a
+    batch, or give its larger pencils the 2-stage route (far fewer launches per pencil)."""
+
+    GRAPH_KERNEL_LIMIT = 1_500_000
+
+    def __init__(self, As, Bs, nstreams=8, precision="fp64_emulated", precisions=None, handle=None, batch_small=128,
+                 sep="1stage", seps=None):
         torch = _torch()
         if len(As) != len(Bs) or len(As) == 0:
             raise ValueError("As and Bs must be non-empty lists of the same length")
@@ -779,51 +843,71 @@ class BatchedSolver:
             _need_matrix(a, f"As[{i}]", square=True, f64=True, cuda=False)
             _need_matrix(b, f"Bs[{i}]", rows=a.shape[0], cols=a.shape[0], f64=True, cuda=False)
             _need_on_device(f"As[{i}]", a, f"Bs[{i}]", b)
+        n = len(As)
+        if precisions is not None and len(precisions) != n:
+            raise ValueError("precisions must give one entry per pencil")
+        if seps is not None and len(seps) != n:
+            raise ValueError("seps must give one entry per pencil")
+        self._own_handle = handle is None
         self.h = handle or Handle()
-        self.count = len(As)
+        self.count = n
         self.As = [a.contiguous() for a in As]
         self.Bs = [b.contiguous() for b in Bs]
         self.M = [int(a.shape[0]) for a in self.As]
         dev = self.As[0].device
         self.w = [torch.empty(m, dtype=torch.float64, device=dev) for m in self.M]
         self.Yt = [torch.empty((m, m), dtype=torch.float64, device=dev) for m in self.M]
-        self.o = make_options(precision=precision, batch_small=batch_small)
         self.nstreams = int(nstreams)
-        n = self.count
+        self.opts = (GepOptions * n)()
+        for i in range(n):
+            self.opts[i] = make_options(precision=precisions[i] if precisions is not None else precision,
+                                        sep=seps[i] if seps is not None else sep, batch_small=batch_small)
         self._M = (ctypes.c_int * n)(*self.M)
         self._A = (_P * n)(*[a.data_ptr() for a in self.As])
         self._B = (_P * n)(*[b.data_ptr() for b in self.Bs])
         self._w = (_P * n)(*[x.data_ptr() for x in self.w])
         self._Y = (_P * n)(*[y.data_ptr() for y in self.Yt])
-        self._prec = None
-        if precisions is not None:
-            self._prec = (ctypes.c_int * n)(*[_PRECS[p] if isinstance(p, str) else int(p) for p in precisions])
         nb = _SZ()
-        _check(self.h.lib.gep_solve_batched_workspace_size(self.h.h, n, self._M, ctypes.byref(self.o), self._prec,
-                                                            self.nstreams, ctypes.byref(nb)),
-               "gep_solve_batched_workspace_size")
+        _check(self.h.lib.gep_solve_batched_opts_workspace_size(self.h.h, n, self._M, self.opts, self.nstreams,
+                                                                 ctypes.byref(nb)),
+               "gep_solve_batched_opts_workspace_size")
         self.h.ensure_workspace(nb.value)
         self.graph = None
+        self.graph_kernels = 0
+        self.eager_kernels = 0
 
     def run(self):
-        _check(self.h.lib.gep_solve_batched(self.h.h, self.count, self._M, self._A, self._B, self._w, self._Y,
-                                            ctypes.byref(self.o), self._prec, self.nstreams), "gep_solve_batched")
+        _check(self.h.lib.gep_solve_batched_opts(self.h.h, self.count, self._M, self._A, self._B, self._w, self._Y,
+                                                 self.opts, self.nstreams), "gep_solve_batched_opts")
 
     def capture(self):
         torch = _torch()
+        self.h.launches(reset=True)
         self.run()  # eager first call creates the child streams outside the capture
         torch.cuda.synchronize()
+        self.eager_kernels = self.h.launches(reset=True)
+        if self.eager_kernels > self.GRAPH_KERNEL_LIMIT:
+            raise ValueError(f"the batch launches {self.eager_kernels} kernels, more than one graph may hold "
+                             f"({self.GRAPH_KERNEL_LIMIT}); split it or give its larger pencils the 2-stage route")
         g = torch.cuda.CUDAGraph()
         s = torch.cuda.Stream()
         _check(self.h.lib.gep_set_stream(self.h.h, ctypes.c_void_p(s.cuda_stream)), "gep_set_stream")
         try:
             with torch.cuda.graph(g, stream=s):
                 self.run()
+            self.graph_kernels = self.h.launches(reset=True)  # kernel launches recorded in the graph
         finally:
             _check(self.h.lib.gep_set_stream(self.h.h, ctypes.c_void_p(self.h.stream.cuda_stream)),
                    "gep_set_stream")
         self.graph = g
         return g
+
+    def close(self):
+        """Releases the graph and, when this solver created it, the handle's workspace."""
+        self.graph = None
+        if self._own_handle:
+            self.h.close()
+            self.h.ws = None
 
     def replay(self):
         self.graph.replay()

@@ -831,14 +831,27 @@ struct BatchPlan {
 
 int small_limit(const gep_options* o) { return o->batch_small < SMALL_MAX ? o->batch_small : SMALL_MAX; }
 
-int make_plan(gep_handle_t h, int count, const int* M, const gep_options* o, const int* prec, int nstreams,
-              BatchPlan* p) {
+// Options of pencil i: opts[i] when given, else o with precision[i] (when given).
+gep_options pencil_opts(const gep_options* o, const int* prec, const gep_options* opts, int i) {
+  if (opts) return opts[i];
+  gep_options oi = *o;
+  if (prec) oi.precision = prec[i];
+  return oi;
+}
+
+int make_plan(gep_handle_t h, int count, const int* M, const gep_options* o, const int* prec,
+              const gep_options* opts, int nstreams, BatchPlan* p) {
   if (count < 0 || count > kMaxBatch) return -2;
   if (nstreams < 1 || nstreams > 64) return -7;
-  if (o->batch_small < 0) return -4;
-  const int small = small_limit(o);
   int order[kMaxBatch];
-  for (int i = 0; i < count; ++i) order[i] = i;
+  bool small_of[kMaxBatch];
+  for (int i = 0; i < count; ++i) {
+    const gep_options oi = pencil_opts(o, prec, opts, i);
+    if (oi.batch_small < 0) return -4;
+    if (M[i] < 0) return -3;
+    order[i] = i;
+    small_of[i] = M[i] >= 1 && M[i] <= small_limit(&oi);
+  }
   for (int a = 1; a < count; ++a) {  // stable insertion sort, M descending
     int t = order[a], b = a - 1;
     while (b >= 0 && M[order[b]] < M[t]) { order[b + 1] = order[b]; --b; }
@@ -846,15 +859,14 @@ int make_plan(gep_handle_t h, int count, const int* M, const gep_options* o, con
   }
   p->nsmall = 0;
   for (int a = 0; a < count; ++a)
-    if (M[order[a]] >= 1 && M[order[a]] <= small) p->small_order[p->nsmall++] = order[a];
+    if (small_of[order[a]]) p->small_order[p->nsmall++] = order[a];
   const int nbig = count - p->nsmall;
   p->ns = nstreams < nbig ? nstreams : (nbig > 0 ? nbig : 1);
   double load[64] = {};
   for (int s = 0; s < 64; ++s) p->need[s] = 0;
   for (int a = 0; a < count; ++a) {
     int i = order[a];
-    if (M[i] < 0) return -3;
-    if (M[i] >= 1 && M[i] <= small) {
+    if (small_of[i]) {
       p->assign[i] = -1;
       continue;
     }
@@ -863,8 +875,7 @@ int make_plan(gep_handle_t h, int count, const int* M, const gep_options* o, con
       if (load[s] < load[best]) best = s;
     p->assign[i] = best;
     load[best] += (double)M[i] * M[i] * M[i];
-    gep_options oi = *o;
-    if (prec) oi.precision = prec[i];
+    const gep_options oi = pencil_opts(o, prec, opts, i);
     size_t need = layout(M[i], &oi).end;
     if (need > p->need[best]) p->need[best] = need;
   }
@@ -880,36 +891,25 @@ int make_plan(gep_handle_t h, int count, const int* M, const gep_options* o, con
   return GEP_OK;
 }
 
-}  // namespace
-
-int gep_solve_batched_workspace_size(gep_handle_t h, int count, const int* M, const gep_options* o,
-                                     const int* precision, int nstreams, size_t* bytes) {
-  if (!handle_ok(h)) return GEP_ERR_HANDLE;
-  if (count > 0 && !M) return -3;
-  if (!o) return -4;
-  if (!bytes) return -7;
+int batched_workspace_size(gep_handle_t h, int count, const int* M, const gep_options* o, const int* prec,
+                           const gep_options* opts, int nstreams, size_t* bytes) {
   static BatchPlan plan;
-  GEP_CHECK(make_plan(h, count, M, o, precision, nstreams, &plan));
+  GEP_CHECK(make_plan(h, count, M, o, prec, opts, nstreams, &plan));
   *bytes = plan.total;
   return GEP_OK;
 }
 
-int gep_solve_batched(gep_handle_t h, int count, const int* M, double* const* A, double* const* B, double* const* w,
-                      double* const* Y, const gep_options* o, const int* precision, int nstreams) {
-  if (!handle_ok(h)) return GEP_ERR_HANDLE;
-  if (count < 0 || count > kMaxBatch) return -2;
-  if (count > 0 && (!M || !A || !B || !w || !Y)) return -3;
-  if (!o) return -8;
-  if (nstreams < 1 || nstreams > 64) return -10;
-  if (o->n_want != 0) return GEP_ERR_UNSUPPORTED;
+int solve_batched(gep_handle_t h, int count, const int* M, double* const* A, double* const* B, double* const* w,
+                  double* const* Y, const gep_options* o, const int* precision, const gep_options* opts,
+                  int nstreams) {
   for (int i = 0; i < count; ++i) {
-    gep_options oi = *o;
-    if (precision) oi.precision = precision[i];
+    const gep_options oi = pencil_opts(o, precision, opts, i);
     GEP_CHECK(check_opts(&oi));
+    if (oi.n_want != 0) return GEP_ERR_UNSUPPORTED;
   }
   if (count == 0) return GEP_OK;
   static BatchPlan plan;
-  GEP_CHECK(make_plan(h, count, M, o, precision, nstreams, &plan));
+  GEP_CHECK(make_plan(h, count, M, o, precision, opts, nstreams, &plan));
   if (h->ws == nullptr || h->ws_bytes < plan.total) return GEP_ERR_ALLOC;
   // child handles, streams and events are created once (outside any stream capture)
   if (!h->fork_ev) GEP_CUDA(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
@@ -934,14 +934,14 @@ int gep_solve_batched(gep_handle_t h, int count, const int* M, double* const* A,
     gep_handle_t c = h->child[s];
     c->ws = h->ws + plan.off[s];
     c->ws_bytes = plan.need[s];
-    gep_options oi = *o;
+    gep_options oi = pencil_opts(o, precision, opts, i);
     oi.timers = 0;
-    if (precision) oi.precision = precision[i];
     GEP_CHECK(gep_solve(c, M[i], A[i], M[i] > 1 ? M[i] : 1, B[i], M[i] > 1 ? M[i] : 1, w[i], Y[i],
                         M[i] > 1 ? M[i] : 1, &oi));
     GEP_CUDA(cudaMemcpyAsync(h->d_batch_info + 2 * i, c->d_status, 2 * sizeof(int), cudaMemcpyDeviceToDevice,
                              c->stream));
-    h->launches += 0;
+    h->launches += c->launches;  // the children's kernel launches count as the batch's
+    c->launches = 0;
   }
   for (int s = 0; s < plan.ns; ++s) {
     GEP_CUDA(cudaEventRecord(h->child_done[s], h->child_stream[s]));
@@ -949,6 +949,48 @@ int gep_solve_batched(gep_handle_t h, int count, const int* M, double* const* A,
   }
   h->batch_count = count;
   return GEP_OK;
+}
+
+}  // namespace
+
+int gep_solve_batched_workspace_size(gep_handle_t h, int count, const int* M, const gep_options* o,
+                                     const int* precision, int nstreams, size_t* bytes) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (count > 0 && !M) return -3;
+  if (!o) return -4;
+  if (!bytes) return -7;
+  return batched_workspace_size(h, count, M, o, precision, nullptr, nstreams, bytes);
+}
+
+int gep_solve_batched(gep_handle_t h, int count, const int* M, double* const* A, double* const* B, double* const* w,
+                      double* const* Y, const gep_options* o, const int* precision, int nstreams) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (count < 0 || count > kMaxBatch) return -2;
+  if (count > 0 && (!M || !A || !B || !w || !Y)) return -3;
+  if (!o) return -8;
+  if (nstreams < 1 || nstreams > 64) return -10;
+  return solve_batched(h, count, M, A, B, w, Y, o, precision, nullptr, nstreams);
+}
+
+int gep_solve_batched_opts_workspace_size(gep_handle_t h, int count, const int* M, const gep_options* opts,
+                                          int nstreams, size_t* bytes) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (count < 0 || count > kMaxBatch) return -2;
+  if (count > 0 && !M) return -3;
+  if (count > 0 && !opts) return -4;
+  if (nstreams < 1 || nstreams > 64) return -5;
+  if (!bytes) return -6;
+  return batched_workspace_size(h, count, M, nullptr, nullptr, opts, nstreams, bytes);
+}
+
+int gep_solve_batched_opts(gep_handle_t h, int count, const int* M, double* const* A, double* const* B,
+                           double* const* w, double* const* Y, const gep_options* opts, int nstreams) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (count < 0 || count > kMaxBatch) return -2;
+  if (count > 0 && (!M || !A || !B || !w || !Y)) return -3;
+  if (count > 0 && !opts) return -8;
+  if (nstreams < 1 || nstreams > 64) return -9;
+  return solve_batched(h, count, M, A, B, w, Y, nullptr, nullptr, opts, nstreams);
 }
 
 int gep_batched_info(gep_handle_t h, int* info) {

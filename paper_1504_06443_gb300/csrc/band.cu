@@ -29,6 +29,9 @@
 // path, its reflectors starting b rows (instead of one) below their column.
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "gep_internal.cuh"
 
 namespace gep {
@@ -917,6 +920,11 @@ int band_to_tridiag(gep_handle_t h, int M, const double* C, int ldc, int b, doub
     // s-1): the time is set by the latency of one step, which co-resident CTAs stretch.
     if (per_sm > BULGE_CTAS_PER_SM) per_sm = BULGE_CTAS_PER_SM;
     int grid = per_sm * h->sm_count;
+    // Sweep s starts two steps after sweep s-1 and lasts about (M - 2) / b + 1 steps, so
+    // about half that many sweeps are in flight at once: CTAs beyond that would only wait,
+    // holding SMs that concurrent solves on other streams could use.
+    const int in_flight = ((M - 2) / b + 1) / 2 + 2;
+    if (grid > in_flight) grid = in_flight;
     if (grid > M - 1) grid = M - 1;
     BulgeArgs a;
     a.M = M; a.b = b; a.ldab = ldab; a.Q = Q; a.AB = AB; a.prog = prog; a.q2 = q2; a.st = h->d_status;
@@ -982,6 +990,40 @@ int build_q2_tiles(gep_handle_t h, cudaStream_t stream, int M, int b, const doub
   return GEP_OK;
 }
 
+// Where U(J, K) - I can be nonzero, per 128-row block of a W x W tile: the reflectors of the
+// tile's diamonds, taken in the order k_q2_tile_build applies them, spread each column's
+// nonzero rows over an interval (a reflector whose rows miss the interval leaves the
+// column alone, one that meets it widens it to the union).  Row block r then needs only
+// the columns whose interval meets its rows.  Every tile has this structure or a subset
+// of it (tiles at the edge hold fewer diamonds).
+static void q2_tile_kranges(int b, OzKRange* kr) {
+  const int W = 2 * TQ * b;
+  std::vector<int> rmin(W), rmax(W);
+  for (int c = 0; c < W; ++c) rmin[c] = rmax[c] = c;
+  for (int jj = TQ - 1; jj >= 0; --jj)
+    for (int kk = 0; kk < TQ; ++kk)
+      for (int c = b - 1; c >= 0; --c) {
+        const int r0 = (jj + kk) * b + c, r1 = r0 + b - 1;
+        for (int x = 0; x < W; ++x)
+          if (r0 <= rmax[x] && r1 >= rmin[x]) {
+            rmin[x] = std::min(rmin[x], r0);
+            rmax[x] = std::max(rmax[x], r1);
+          }
+      }
+  kr->n = std::min((W + 127) / 128, OZ_KR_MAX);
+  for (int r = 0; r < kr->n; ++r) {
+    const int a = 128 * r, e = std::min(W, a + 128) - 1;
+    int lo = W, hi = 0;
+    for (int x = 0; x < W; ++x)
+      if (rmin[x] <= e && rmax[x] >= a) {
+        lo = std::min(lo, x);
+        hi = std::max(hi, x + 1);
+      }
+    kr->lo[r] = lo < hi ? lo : 0;
+    kr->hi[r] = lo < hi ? hi : 0;
+  }
+}
+
 // Z (M x ncol) <- Q2 Z.  engine FP64: diamonds applied directly on the FP64 cores.
 // Otherwise the diamonds are merged into dense W x W tiles U(J, R) and every tile is
 // applied as one product Z(rows) <- U Z(rows) on the engine (ws: q2_tile_ws_elems).
@@ -998,6 +1040,8 @@ int apply_q2(gep_handle_t h, int M, int b, const double* q2, double* Z, int ldz,
     double* Ubuf = ws;
     double* Tmp = ws + rr((size_t)(Q / TQ + 1) * W * W);
     size_t smem = q2_tile_smem_bytes(b);
+    OzKRange kr;
+    q2_tile_kranges(b, &kr);
     GEP_CHECK(set_tile_build_attr());
     for (int J = nJ - 1; J >= 0; --J) {
       const int nK = (Q - J * TQ) / TQ + 1;  // tiles (J, K) with a diamond: K TQ <= Q - J TQ
@@ -1018,10 +1062,10 @@ int apply_q2(gep_handle_t h, int M, int b, const double* q2, double* Z, int ldz,
         // before its product kernel writes C, so the update may run in place
         const size_t one_panel = (size_t)16 * (Wc + ncol) * ((Wc + 31) / 32 * 32) + (size_t)4 * (Wc + ncol) + 4096;
         if (Wc >= 128 && ncol >= 64 && Wc <= 4096 && one_panel <= h->eng_bytes) {
-          GEP_CHECK(dgemm(h, 'N', 'N', 'F', Wc, ncol, Wc, 1.0, Ut, W, Z + r0, ldz, 1.0, Z + r0, ldz, engine));
+          GEP_CHECK(dgemm(h, 'N', 'N', 'F', Wc, ncol, Wc, 1.0, Ut, W, Z + r0, ldz, 1.0, Z + r0, ldz, engine, &kr));
         } else {  // Z(rows) += (U - I) copy(Z(rows))
           GEP_CHECK(copy_matrix(h, Wc, ncol, Z + r0, ldz, Tmp, Wc));
-          GEP_CHECK(dgemm(h, 'N', 'N', 'F', Wc, ncol, Wc, 1.0, Ut, W, Tmp, Wc, 1.0, Z + r0, ldz, engine));
+          GEP_CHECK(dgemm(h, 'N', 'N', 'F', Wc, ncol, Wc, 1.0, Ut, W, Tmp, Wc, 1.0, Z + r0, ldz, engine, &kr));
         }
       }
     }

@@ -242,16 +242,16 @@ int dgemm_f64(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, 
 
 int dgemm(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, double alpha,
           const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
-          int engine) {
+          int engine, const OzKRange* kr) {
   // Products too small to fill 128 x 64 tensor-core tiles stay on the FP64 FMA kernel, and
   // so do outputs of one or two tiles with a long K (split K over many CTAs there).
   bool big = m >= 128 && n >= 64 && k >= 16;
   const long long oz_tiles = (long long)((m + 127) / 128) * ((n + 63) / 64);
   if (big && oz_tiles <= 2 && k >= 2048) big = false;
   if (engine == GEP_PREC_FP64_EMULATED && big)
-    return dgemm_oz(h, ta, tb, uplo, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 9);
+    return dgemm_oz(h, ta, tb, uplo, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 9, kr);
   if (engine == GEP_PREC_MIXED_REFINED && big)
-    return dgemm_oz(h, ta, tb, uplo, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 4);
+    return dgemm_oz(h, ta, tb, uplo, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 4, kr);
   return dgemm_f64(h, ta, tb, uplo, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 

@@ -39,7 +39,11 @@ namespace gep {
 namespace {
 
 constexpr int TM = 128, TN = 64, TK = 32, KCH = 512, STAGES = 2, MAXS = 8;
-constexpr int NTHREADS = 320;
+// warp 0 issues the TMA loads, warp 1 the MMAs; EPI_WARPS warps drain the accumulators
+// (four per 32-lane quarter of TMEM, each with CPW of the tile's TN columns): the drain
+// stalls the MMAs, and more warps per scheduler hide its TMEM-load and conversion latency
+constexpr int EPI_WARPS = 16, CPW = TN / (EPI_WARPS / 4);
+constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
 constexpr int KP_MAX = 4096;  // K panel per launch (integer accumulators sized for <= 16 chunks)
 
 // ------------------------------------------------------------------ splitting
@@ -353,6 +357,19 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
+// 32 lanes x 16 consecutive 32-bit columns of TMEM from taddr; waits for the load
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
   asm volatile(
@@ -366,6 +383,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v) {
+  if constexpr (N == 16) tmem_ld16(taddr, v);
+  else tmem_ld32(taddr, v);
 }
 
 // T = hi * 2^D + lo as a 128-bit two's-complement integer (0 <= D < 64), returned
@@ -435,6 +458,10 @@ constexpr int GROUP_M = 8;  // row tiles per group of the tile order (L2 reuse o
 struct OzArgs {
   int m, n, kpad, S, lmax, lower, xbit;
   int gx, gy, ntiles;  // tile grid gx x gy (128-row x 64-column tiles), in grouped order
+  // kr_n > 0: row tile r < kr_n runs only the k-steps [kr_lo[r], kr_hi[r]) of this panel
+  // (op(A) is exactly zero elsewhere in its rows); other row tiles run all of them
+  int kr_n;
+  short kr_lo[OZ_KR_MAX], kr_hi[OZ_KR_MAX];
   const int* ea;
   const int* eb;
   double alpha, beta;
@@ -454,8 +481,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__
   __shared__ uint32_t tmem_slot;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ int skip;
-  // persistent: CTA b takes tiles b, b + gridDim.x, ...; tiles strictly above the
-  // diagonal of a lower-triangle product are skipped by every role alike.  Tiles are
+  __shared__ short kr_lo[OZ_KR_MAX], kr_hi[OZ_KR_MAX];
+  // persistent: in wave i CTA b takes tile i G + (b + i) mod G (G = gridDim.x; the last,
+  // partial wave unrotated), so a CTA does not meet the same row tile in every wave when G
+  // is a multiple of the row-tile count (row tiles may differ in work, see kr_lo / kr_hi);
+  // tiles strictly above the diagonal of a lower-triangle product are skipped by every
+  // role alike.  Tiles are
   // numbered in groups of GROUP_M row tiles, row fastest inside a group: the tiles that run
   // at the same time cover a near-square block of C (8 rows x ~19 columns on 152 SMs), so
   // their A and B planes are read from DRAM about once and then hit in L2.
@@ -468,6 +499,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__
     tn = (local / gm) * TN;
     return !(p.lower && tm + TM - 1 < tn);
   };
+  auto tile_of = [&](int i) {
+    const int G = gridDim.x, base = i * G;
+    return base + G <= p.ntiles ? base + (int)((blockIdx.x + i) % G) : base + (int)blockIdx.x;
+  };
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int S = SC > 0 ? SC : p.S, LMAX = LC > 0 ? LC : p.lmax;
   const uint32_t a_bytes = (uint32_t)S * TM * TK * 2, b_bytes = (uint32_t)S * TN * TK * 2;
@@ -476,17 +511,32 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__
   const uint32_t bar_accf = smem_u32(&bars[2 * STAGES]), bar_acce = smem_u32(&bars[2 * STAGES + 1]);
   const uint32_t bar_done = smem_u32(&bars[2 * STAGES + 2]);
   const int nsteps = p.kpad / TK;
-  const int nchunks = (p.kpad + KCH - 1) / KCH;
   const int nlev = LMAX - 1;  // levels 2..LMAX
+  // the k-steps [s0, s1) of the tile whose first row is tm (every role takes the same)
+  auto tile_steps = [&](int tm, int& s0, int& s1) {
+    s0 = 0;
+    s1 = nsteps;
+    const int r = tm / TM;
+    if (r < p.kr_n) {
+      s0 = kr_lo[r];
+      s1 = kr_hi[r];
+    }
+  };
+  constexpr int SPC = KCH / TK;  // k-steps per exactly accumulated chunk
 
   if (threadIdx.x == 0) {
     skip = status_bad(p.st) ? 1 : 0;
+#pragma unroll
+    for (int i = 0; i < OZ_KR_MAX; ++i) {
+      kr_lo[i] = p.kr_lo[i];
+      kr_hi[i] = p.kr_hi[i];
+    }
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(bar_full + 8 * s, 1);
       mbar_init(bar_empty + 8 * s, 1);
     }
     mbar_init(bar_accf, 1);
-    mbar_init(bar_acce, 8);
+    mbar_init(bar_acce, EPI_WARPS);
     mbar_init(bar_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -509,10 +559,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__
     if (lane == 0) {
       int g = 0;  // k-steps issued by this CTA over all its tiles
       bool ok = true;
-      for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-        int tm, tn;
+      for (int i = 0, t; ok && (t = tile_of(i)) < p.ntiles; ++i) {
+        int tm, tn, s0, s1;
         if (!tile_rc(t, tm, tn)) continue;
-        for (int step = 0; step < nsteps && ok; ++step, ++g) {
+        tile_steps(tm, s0, s1);
+        for (int step = s0; step < s1 && ok; ++step, ++g) {
           int sidx = g % STAGES;
           uint32_t ph = (uint32_t)(g / STAGES) & 1u;
           ok = mbar_wait(bar_empty + 8 * sidx, ph ^ 1u, p.st);
@@ -531,15 +582,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__
     if (lane == 0) {
       bool ok = true;
       int g = 0, gc = 0;  // k-steps and chunks consumed over all tiles
-      for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-      int tm, tn;
+      for (int i = 0, t; ok && (t = tile_of(i)) < p.ntiles; ++i) {
+      int tm, tn, s0, s1;
       if (!tile_rc(t, tm, tn)) continue;
-      int step = 0;
-      for (int c = 0; c < nchunks && ok; ++c, ++gc) {
+      tile_steps(tm, s0, s1);
+      const int nch = (s1 - s0 + SPC - 1) / SPC;
+      int step = s0;
+      for (int c = 0; c < nch && ok; ++c, ++gc) {
         ok = mbar_wait(bar_acce, ((uint32_t)gc & 1u) ^ 1u, p.st);
         if (!ok) break;
         tc_fence_after();
-        int send = min(nsteps, (c + 1) * (KCH / TK));
+        int send = min(s1, s0 + (c + 1) * SPC);
         for (int sic = 0; step < send; ++step, ++sic, ++g) {
           int sidx = g % STAGES;
           ok = mbar_wait(bar_full + 8 * sidx, (uint32_t)(g / STAGES) & 1u, p.st);
@@ -577,34 +630,36 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__
       mbar_wait(bar_done, 0, p.st);
     }
   } else {
-    // epilogue: warp w reads TMEM lanes 32*(w%4).., columns 32*((w-2)/4)..
-    const int q = warp & 3, half = (warp - 2) >> 2;
+    // epilogue: warp w reads TMEM lanes 32*(w%4).., columns CPW*((w-2)/4)..
+    const int q = warp & 3, cg = (warp - 2) >> 2;
     bool ok = true;
     int gc = 0;
-    for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-    int tm, tn;
+    for (int i = 0, t; ok && (t = tile_of(i)) < p.ntiles; ++i) {
+    int tm, tn, s0, s1;
     if (!tile_rc(t, tm, tn)) continue;
+    tile_steps(tm, s0, s1);
+    const int nch = (s1 - s0 + SPC - 1) / SPC;
     const int row = tm + q * 32 + lane;
-    long long hi[32], lo[32];
+    long long hi[CPW], lo[CPW];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) { hi[j] = 0; lo[j] = 0; }
-    for (int c = 0; c < nchunks; ++c, ++gc) {
+    for (int j = 0; j < CPW; ++j) { hi[j] = 0; lo[j] = 0; }
+    for (int c = 0; c < nch; ++c, ++gc) {
       ok = mbar_wait(bar_accf, (uint32_t)gc & 1u, p.st);
       if (!ok) break;
       tc_fence_after();
 #pragma unroll 1
       for (int lv = 0; lv < nlev; ++lv) {
         int l = lv + 2;
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(lv * TN + half * 32), v);
+        float v[CPW];
+        tmem_ld<CPW>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(lv * TN + cg * CPW), v);
         if (l <= 4) {
           int sh = 7 * (4 - l);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) hi[j] += (long long)__float2int_rn(v[j]) * (1ll << sh);
+          for (int j = 0; j < CPW; ++j) hi[j] += (long long)__float2int_rn(v[j]) * (1ll << sh);
         } else {
           int sh = 7 * (LMAX - l);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) lo[j] += (long long)__float2int_rn(v[j]) * (1ll << sh);
+          for (int j = 0; j < CPW; ++j) lo[j] += (long long)__float2int_rn(v[j]) * (1ll << sh);
         }
       }
       tc_fence_before();
@@ -618,8 +673,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(const __grid_constant__
       const int base_adj = ea - (two ? 7 * LMAX : 28);
       const double alpha = p.alpha, beta = p.beta;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        int col = tn + half * 32 + j;
+      for (int j = 0; j < CPW; ++j) {
+        int col = tn + cg * CPW + j;
         if (col >= p.n || (p.lower && row < col)) continue;
         double v = fixed_to_double(hi[j], two ? lo[j] : 0ll, D, base_adj + scale_exp(p.eb[col], p.xbit));
         double* cp = p.C + (size_t)row + (size_t)col * p.ldc;
@@ -688,7 +743,7 @@ size_t oz_workspace_bytes(int m, int n, int k) {
 }
 
 int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, double alpha, const double* A,
-             int lda, const double* B, int ldb, double beta, double* C, int ldc, int levels) {
+             int lda, const double* B, int ldb, double beta, double* C, int ldc, int levels, const OzKRange* kr) {
   if (m <= 0 || n <= 0) return GEP_OK;
   if (k <= 0 || alpha == 0.0) return dgemm_f64(h, ta, tb, uplo, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
   const int S = levels - 1;
@@ -773,6 +828,17 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
     a.gx = gx;
     a.gy = gy;
     a.ntiles = gx * gy;
+    a.kr_n = 0;
+    for (int r = 0; r < OZ_KR_MAX; ++r) a.kr_lo[r] = a.kr_hi[r] = 0;
+    if (kr && kr->n > 0) {  // this panel's k-steps of each listed row tile
+      a.kr_n = min(min(kr->n, OZ_KR_MAX), gx);
+      for (int r = 0; r < a.kr_n; ++r) {
+        int lo = max(kr->lo[r] - kb, 0), hi = min(kr->hi[r] - kb, kc);
+        if (hi <= lo) lo = hi = 0;
+        a.kr_lo[r] = (short)(lo / TK);
+        a.kr_hi[r] = (short)((hi + TK - 1) / TK);
+      }
+    }
     dim3 grid(a.ntiles < h->sm_count ? a.ntiles : h->sm_count);  // persistent CTAs
     int slot = -1;
     if (h->prof_on) {

@@ -115,15 +115,23 @@ inline int check_launch(gep_handle_t h) {
   } while (0)
 
 // ---- dense contraction engines (gemm_f64.cu, gemm_oz.cu) ----
+// Structure of op(A) a product may exploit: rows [128 r, 128 r + 128) of op(A) are exactly
+// zero outside the columns [lo[r], hi[r]) for r < n (the other row blocks are dense).  The
+// split-BF16 engine skips the zero part (same result bits); the FP64 engine ignores it.
+constexpr int OZ_KR_MAX = 32;
+struct OzKRange {
+  int n = 0;
+  int lo[OZ_KR_MAX], hi[OZ_KR_MAX];
+};
 // C = alpha op(A) op(B) + beta C; uplo 'L' restricts computation/storage to i >= j.
 int dgemm(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, double alpha,
           const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
-          int engine);
+          int engine, const OzKRange* kr = nullptr);
 int dgemm_f64(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, double alpha,
               const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc);
 int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, double alpha,
              const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
-             int levels);
+             int levels, const OzKRange* kr = nullptr);
 size_t oz_workspace_bytes(int m, int n, int k);
 
 // ---- small dense helpers (blas_util.cu) ----

@@ -80,6 +80,13 @@ def test_host_checks_without_gpu(libpath):
     lib.gep_get_info.restype = ctypes.c_int
     v = ctypes.c_int(7)
     assert lib.gep_get_info(None, ctypes.byref(v)) == -104
+    lib.gep_solve_batched_opts.argtypes = [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 6 + [ctypes.c_int]
+    lib.gep_solve_batched_opts.restype = ctypes.c_int
+    assert lib.gep_solve_batched_opts(None, 0, None, None, None, None, None, None, 1) == -104
+    lib.gep_solve_batched_opts_workspace_size.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                                          ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    lib.gep_solve_batched_opts_workspace_size.restype = ctypes.c_int
+    assert lib.gep_solve_batched_opts_workspace_size(None, 0, None, None, 1, None) == -104
     lib.sep_q2_elems.argtypes = [ctypes.c_int, ctypes.c_int]
     lib.sep_q2_elems.restype = ctypes.c_size_t
     assert lib.sep_q2_elems(100, 0) == 0 and lib.sep_q2_elems(1, 8) == 0

@@ -38,7 +38,7 @@ def test_batched_eager_and_graph_match_single(gep):
     orders = gi.batch_orders(12, seed=77, lo=64, hi=384)
     As, Bs = _batch(1000, orders)
     precisions = ["fp64_emulated" if M >= 256 else "fp64" for M in orders]
-    bs = gep.BatchedSolver(As, Bs, nstreams=4, precisions=precisions)
+    bs = gep.BatchedSolver(As, Bs, nstreams=4, precisions=precisions, batch_small=0)
     bs.run()
     torch.cuda.synchronize()
     assert bs.info() == 0
@@ -117,7 +117,7 @@ def test_batched_workload_shapes_vs_oracle(gep, batch_vs_oracle, precision):
     orders, pencils = batch_vs_oracle
     As = [dev(p["A"]) for p in pencils]
     Bs = [dev(p["B"]) for p in pencils]
-    bs = gep.BatchedSolver(As, Bs, nstreams=8, precision=precision)
+    bs = gep.BatchedSolver(As, Bs, nstreams=8, precision=precision, batch_small=0)
     bs.run()
     torch.cuda.synchronize()
     assert bs.info() == 0
@@ -189,3 +189,69 @@ def test_autotuner_small_choice(gep):
     tuner = gep.Autotuner()
     tuner.tune(As[:1] + As2, Bs[:1] + Bs2, reps=1)
     assert tuner.tune_small(As + As2, Bs + Bs2) in (0, 128)
+
+
+def test_batched_per_pencil_routes_vs_oracle(gep, batch_vs_oracle):
+    """Per-pencil options (gep_solve_batched_opts): the larger pencils on the 2-stage route,
+    the others 1-stage, one-CTA route for order <= 128; eager and replayed from a graph,
+    every pencil against the oracle at the FP64 tolerances."""
+    import torch
+    orders, pencils = batch_vs_oracle
+    As = [dev(p["A"]) for p in pencils]
+    Bs = [dev(p["B"]) for p in pencils]
+    seps = ["2stage" if M >= 256 else "1stage" for M in orders]
+    bs = gep.BatchedSolver(As, Bs, nstreams=6, precision="fp64_emulated", seps=seps, batch_small=128)
+    bs.run()
+    torch.cuda.synchronize()
+    assert bs.info() == 0
+    _check_against_oracle(bs.results(), pencils, "eager")
+    bs.capture()
+    assert 0 < bs.graph_kernels <= bs.eager_kernels + 64
+    for w, Yt in zip(bs.w, bs.Yt):
+        w.zero_()
+        Yt.zero_()
+    bs.replay()
+    torch.cuda.synchronize()
+    assert bs.info() == 0
+    _check_against_oracle(bs.results(), pencils, "graph")
+
+
+def test_batched_legacy_entry_matches_per_pencil_options(gep):
+    """gep_solve_batched (one options struct plus a precision per pencil) and
+    gep_solve_batched_opts with the equivalent per-pencil structs give the same bits."""
+    import ctypes
+    import torch
+    orders = [300, 64, 520, 140, 96]
+    As, Bs = _batch(4100, orders)
+    precs = ["fp64_emulated" if M >= 256 else "fp64" for M in orders]
+    bs = gep.BatchedSolver(As, Bs, nstreams=3, precisions=precs, batch_small=100)
+    bs.run()
+    torch.cuda.synchronize()
+    ref = [(w.clone(), Yt.clone()) for w, Yt in zip(bs.w, bs.Yt)]
+    n = len(orders)
+    o = gep.make_options(precision="fp64_emulated", batch_small=100)
+    prec = (ctypes.c_int * n)(*[gep._PRECS[p] for p in precs])
+    for w, Yt in zip(bs.w, bs.Yt):
+        w.zero_()
+        Yt.zero_()
+    rc = bs.h.lib.gep_solve_batched(bs.h.h, n, bs._M, bs._A, bs._B, bs._w, bs._Y, ctypes.byref(o), prec, 3)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert bs.info() == 0
+    for (w0, Y0), w, Yt in zip(ref, bs.w, bs.Yt):
+        assert torch.equal(w0, w) and torch.equal(Y0, Yt)
+
+
+def test_batched_capture_refuses_oversized_graph(gep):
+    """A batch whose eager run launches more kernels than the graph limit is not captured
+    (the solver raises before recording anything) and still runs eagerly."""
+    import torch
+    As, Bs = _batch(4200, [200, 160])
+    bs = gep.BatchedSolver(As, Bs, nstreams=2, batch_small=0)
+    bs.GRAPH_KERNEL_LIMIT = 10
+    with pytest.raises(ValueError):
+        bs.capture()
+    assert bs.graph is None and bs.eager_kernels > 10
+    bs.run()
+    torch.cuda.synchronize()
+    assert bs.info() == 0
