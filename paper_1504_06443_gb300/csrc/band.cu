@@ -729,8 +729,11 @@ size_t q2_elems(int M, int b) {
 
 size_t band_ws_elems(int M, int b) {
   size_t G = pqr_partial_ctas(M);
+  // + the digit planes of the trailing matrix (shared by the two C22 products of a panel
+  // pair) and [0; V1] (M x b)
   size_t reduce = 2 * rr(G * BMAX) + 2 * rr(BMAX) + rr(32) + 4 * rr((size_t)M * b) + rr((size_t)M * 3 * b) +
-                  2 * rr((size_t)M * 4 * b) + 6 * rr((size_t)2 * b * b);
+                  2 * rr((size_t)M * 4 * b) + 6 * rr((size_t)2 * b * b) +
+                  rr(oz_sym_planes_bytes(M, 9) / sizeof(double) + 1) + rr((size_t)M * b);
   size_t chase = rr((size_t)2 * b * M) + rr((size_t)M);  // band + progress counters
   return reduce > chase ? reduce : chase;
 }
@@ -743,6 +746,9 @@ struct BandWs {
   int* bar;
   double *V, *CV, *WVW, *V1, *W1, *AA, *BB;
   double *GV, *T, *Tt, *Pm, *Ym, *Zs;
+  double* Vpad;        // [0; V1], n x b
+  void* planes;        // digit planes of C22
+  size_t planes_bytes;
 };
 
 // QR of the n x b panel P (ld ldp): reflectors stay in P, tau[0..b), explicit V (n x b,
@@ -851,13 +857,26 @@ int band_reduce(gep_handle_t h, int M, double* C, int ldc, int b, double* tau1, 
   w.Pm = take((size_t)2 * b * b);
   w.Ym = take((size_t)2 * b * b);
   w.Zs = take((size_t)2 * b * b);
+  w.Vpad = take((size_t)M * b);
+  w.planes_bytes = oz_sym_planes_bytes(M, 9);
+  w.planes = take(w.planes_bytes / sizeof(double) + 1);
+  const int levels = eng == GEP_PREC_MIXED_REFINED ? 4 : 9;
   for (int pb = 0; M - pb - b >= 2;) {
     const int n = M - pb - b;
     double* P = C + (pb + b) + (size_t)pb * ldc;
     double* C22 = C + (pb + b) + (size_t)(pb + b) * ldc;
     double* W = w.WVW;  // [W | V | W]
     GEP_CHECK(panel_factor(h, n, b, P, ldc, tau1 + pb, w, w.V, eng));
-    GEP_CHECK(dgemm(h, 'S', 'N', 'F', n, b, n, 1.0, C22, ldc, w.V, n, 0.0, w.CV, n, eng));  // C22 V
+    // C22 V.  On the tensor-core engines C22 is split into digit planes once and the planes
+    // serve C22b V1 below as well (C22b = C22(b:, b:) is not changed in between).
+    OzSymPlanes planes;
+    const bool use_planes = eng != GEP_PREC_FP64 && n >= 128 && b >= 64;
+    if (use_planes) {
+      GEP_CHECK(oz_split_sym(h, n, C22, ldc, levels, w.planes, w.planes_bytes, &planes));
+      GEP_CHECK(dgemm_oz_sym_planes(h, planes, 0, b, 1.0, w.V, n, 0.0, w.CV, n));
+    } else {
+      GEP_CHECK(dgemm(h, 'S', 'N', 'F', n, b, n, 1.0, C22, ldc, w.V, n, 0.0, w.CV, n, eng));
+    }
     GEP_CHECK(panel_w(h, n, b, w.V, w.CV, W, w, eng));
     GEP_CHECK(copy_matrix(h, n, b, w.V, n, w.WVW + (size_t)n * b, n));
     GEP_CHECK(copy_matrix(h, n, b, W, n, w.WVW + (size_t)2 * n * b, n));
@@ -875,7 +894,15 @@ int band_reduce(gep_handle_t h, int M, double* C, int ldc, int b, double* tau1, 
                     eng));
     GEP_CHECK(panel_factor(h, n1, b, P1, ldc, tau1 + pb + b, w, w.V1, eng));
     double* C22b = C22 + b + (size_t)b * ldc;  // not yet updated by panel p
-    GEP_CHECK(dgemm(h, 'S', 'N', 'F', n1, b, n1, 1.0, C22b, ldc, w.V1, n1, 0.0, w.CV, n1, eng));
+    if (use_planes && n1 >= 128) {
+      // C22b V1 = rows b.. of C22 times [0; V1]: the planes' columns 0..b-1 (panel p+1, since
+      // updated) meet zeros
+      GEP_CHECK(set_matrix(h, b, b, 0.0, 0.0, w.Vpad, n));
+      GEP_CHECK(copy_matrix(h, n1, b, w.V1, n1, w.Vpad + b, n));
+      GEP_CHECK(dgemm_oz_sym_planes(h, planes, b, b, 1.0, w.Vpad, n, 0.0, w.CV, n1));
+    } else {
+      GEP_CHECK(dgemm(h, 'S', 'N', 'F', n1, b, n1, 1.0, C22b, ldc, w.V1, n1, 0.0, w.CV, n1, eng));
+    }
     // Zs = [V' W']^T V1 (2b x b), CV -= [W' V'] Zs  (' = rows b.. of panel p's V, W)
     GEP_CHECK(dgemm(h, 'T', 'N', 'F', 2 * b, b, n1, 1.0, w.WVW + (size_t)n * b + b, n, w.V1, n1, 0.0, w.Zs, 2 * b,
                     eng));

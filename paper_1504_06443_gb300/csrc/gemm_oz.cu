@@ -714,9 +714,12 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-int encode_map(CUtensorMap* map, const void* base, int kpad, int rows, int S, int box_rows) {
+// plane_rows: rows between consecutive planes (0: rows), for a view of the last rows of
+// a plane set
+int encode_map(CUtensorMap* map, const void* base, int kpad, int rows, int S, int box_rows, int plane_rows = 0) {
+  if (plane_rows <= 0) plane_rows = rows;
   cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)S};
-  cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)kpad * 2 * (cuuint64_t)rows};
+  cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)kpad * 2 * (cuuint64_t)plane_rows};
   cuuint32_t box[3] = {(cuuint32_t)TK, (cuuint32_t)box_rows, (cuuint32_t)S};
   cuuint32_t estr[3] = {1, 1, 1};
   EncodeTiledFn enc = encode_fn();
@@ -735,6 +738,123 @@ int encode_map(CUtensorMap* map, const void* base, int kpad, int rows, int S, in
 }
 
 }  // namespace
+
+namespace {
+
+// Product-kernel launch for one K panel (kc deep, planes padded to a.kpad): dynamic shared
+// memory attribute, optional per-launch timing, template dispatch on the plane/level counts.
+int oz_launch(gep_handle_t h, const CUtensorMap& mA, const CUtensorMap& mB, const OzArgs& a, int kc) {
+  static unsigned long long attr_devices = 0;
+  if (first_use_on_device(attr_devices)) {
+    cudaFuncSetAttribute(k_oz_gemm<8, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes_for(MAXS));
+    cudaFuncSetAttribute(k_oz_gemm<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes_for(MAXS));
+    cudaFuncSetAttribute(k_oz_gemm<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes_for(MAXS));
+  }
+  const int S = a.S, levels = a.lmax;
+  dim3 grid(a.ntiles < h->sm_count ? a.ntiles : h->sm_count);  // persistent CTAs
+  int slot = -1;
+  if (h->prof_on) {
+    if (h->prof_used < h->prof_cap) {
+      slot = h->prof_used++;
+      cudaEventRecord(h->prof_ev[2 * slot], h->stream);
+      int npairs = 0;
+      for (int s = 1; s <= S; ++s) npairs += max(0, min(S, levels - s));
+      double f = 2.0 * a.m * a.n * (double)kc * (a.lower ? 0.5 : 1.0);
+      h->prof_f64eq[slot] = f;
+      h->prof_flops[slot] = f * npairs;
+      h->prof_mnk[3 * slot] = a.m;
+      h->prof_mnk[3 * slot + 1] = a.n;
+      h->prof_mnk[3 * slot + 2] = kc;
+    } else {
+      h->prof_skipped++;
+    }
+  }
+  if (S == 8 && levels == 9) k_oz_gemm<8, 9><<<grid, NTHREADS, smem_bytes_for(S), h->stream>>>(mA, mB, a);
+  else if (S == 3 && levels == 4) k_oz_gemm<3, 4><<<grid, NTHREADS, smem_bytes_for(S), h->stream>>>(mA, mB, a);
+  else k_oz_gemm<0, 0><<<grid, NTHREADS, smem_bytes_for(S), h->stream>>>(mA, mB, a);
+  GEP_CHECK(check_launch(h));
+  if (slot >= 0) cudaEventRecord(h->prof_ev[2 * slot + 1], h->stream);
+  return GEP_OK;
+}
+
+void oz_args_init(OzArgs& a, int m, int n, int kpad, int S, int levels, int lower, int xbit, const int* ea,
+                  const int* eb, double alpha, double beta, double* C, int ldc, int* st) {
+  a.m = m; a.n = n; a.kpad = kpad; a.S = S; a.lmax = levels; a.lower = lower; a.xbit = xbit;
+  a.ea = ea; a.eb = eb; a.alpha = alpha; a.beta = beta; a.C = C; a.ldc = ldc; a.st = st;
+  a.gx = (m + TM - 1) / TM;
+  a.gy = (n + TN - 1) / TN;
+  a.ntiles = a.gx * a.gy;
+  a.kr_n = 0;
+  for (int r = 0; r < OZ_KR_MAX; ++r) a.kr_lo[r] = a.kr_hi[r] = 0;
+}
+
+}  // namespace
+
+size_t oz_sym_planes_bytes(int m, int levels) {
+  if (m <= 0) return 0;
+  const size_t S = (size_t)(levels - 1), np = (m + OZ_SYM_KP - 1) / OZ_SYM_KP;
+  const size_t kpad_last = (size_t)((m - (np - 1) * OZ_SYM_KP + TK - 1) / TK) * TK;
+  return align256((size_t)2 * S * m * ((np - 1) * OZ_SYM_KP + kpad_last)) + align256(sizeof(int) * np * m) + 256;
+}
+
+int oz_split_sym(gep_handle_t h, int m, const double* A, int lda, int levels, void* buf, size_t bytes,
+                 OzSymPlanes* P) {
+  const int S = levels - 1;
+  if (S < 1 || S > MAXS || m <= 0) return GEP_ERR_UNSUPPORTED;
+  if (buf == nullptr || bytes < oz_sym_planes_bytes(m, levels)) return GEP_ERR_ALLOC;
+  const int np = (m + OZ_SYM_KP - 1) / OZ_SYM_KP;
+  const int kpad_last = (m - (np - 1) * OZ_SYM_KP + TK - 1) / TK * TK;
+  P->planes = (unsigned short*)buf;
+  P->ea = (int*)((char*)buf + align256((size_t)2 * S * m * ((size_t)(np - 1) * OZ_SYM_KP + kpad_last)));
+  P->m = m;
+  P->levels = levels;
+  const int xbit = levels >= 8 ? 1 : 0;
+  GEP_CUDA(cudaMemsetAsync(P->ea, 0, sizeof(int) * (size_t)np * m, h->stream));
+  for (int p = 0; p < np; ++p) {
+    const int kb = p * OZ_SYM_KP, kc = min(OZ_SYM_KP, m - kb), kpad = (kc + TK - 1) / TK * TK;
+    int* ea = P->ea + (size_t)p * m;
+    unsigned short* As = P->planes + (size_t)p * S * m * OZ_SYM_KP;
+    k_rowexp_sym_row<<<dim3((m + 255) / 256, (kc + 63) / 64), 256, 0, h->stream>>>(m, kb, kc, A, lda, ea,
+                                                                                  h->d_status);
+    GEP_CHECK(check_launch(h));
+    k_rowexp_sym_col<<<(m * 32 + 255) / 256, 256, 0, h->stream>>>(m, kb, kc, A, lda, ea, h->d_status);
+    GEP_CHECK(check_launch(h));
+    k_split_sym<<<dim3(kpad / 32, (m + 31) / 32), 256, 0, h->stream>>>(m, kc, kpad, kb, A, lda, ea, S, xbit, As,
+                                                                       h->d_status);
+    GEP_CHECK(check_launch(h));
+  }
+  return GEP_OK;
+}
+
+int dgemm_oz_sym_planes(gep_handle_t h, const OzSymPlanes& P, int row0, int n, double alpha, const double* B,
+                        int ldb, double beta, double* C, int ldc) {
+  const int m = P.m - row0, S = P.levels - 1, K = P.m;
+  if (row0 < 0 || m <= 0 || n <= 0) return GEP_OK;
+  if (S < 1 || S > MAXS || !P.planes) return GEP_ERR_UNSUPPORTED;
+  const int kp_max = K < OZ_SYM_KP ? K : OZ_SYM_KP;
+  const int kpad_max = (kp_max + TK - 1) / TK * TK;
+  const size_t need = align256((size_t)2 * S * n * kpad_max) + align256(sizeof(int) * (size_t)n) + 256;
+  if (h->eng_ws == nullptr || h->eng_bytes < need) return GEP_ERR_ALLOC;
+  unsigned short* Bs = (unsigned short*)h->eng_ws;
+  int* eb = (int*)(h->eng_ws + align256((size_t)2 * S * n * kpad_max));
+  const int xbit = P.levels >= 8 ? 1 : 0;
+  const int np = (K + OZ_SYM_KP - 1) / OZ_SYM_KP;
+  for (int p = 0; p < np; ++p) {
+    const int kb = p * OZ_SYM_KP, kc = min(OZ_SYM_KP, K - kb), kpad = (kc + TK - 1) / TK * TK;
+    const unsigned short* As = P.planes + (size_t)p * S * P.m * OZ_SYM_KP;
+    k_split_rows<<<(n * 32 + 255) / 256, 256, 0, h->stream>>>(n, kc, kpad, B + kb, ldb, eb, S, xbit, Bs,
+                                                              h->d_status);
+    GEP_CHECK(check_launch(h));
+    CUtensorMap mA, mB;
+    GEP_CHECK(encode_map(&mA, As + (size_t)row0 * kpad, kpad, m, S, TM, P.m));  // rows row0.. of each plane
+    GEP_CHECK(encode_map(&mB, Bs, kpad, n, S, TN));
+    OzArgs a;
+    oz_args_init(a, m, n, kpad, S, P.levels, 0, xbit, P.ea + (size_t)p * P.m + row0, eb, alpha,
+                 p == 0 ? beta : 1.0, C, ldc, h->d_status);
+    GEP_CHECK(oz_launch(h, mA, mB, a, kc));
+  }
+  return GEP_OK;
+}
 
 size_t oz_workspace_bytes(int m, int n, int k) {
   int kp = k < KP_MAX ? k : KP_MAX;
@@ -764,12 +884,6 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
   long long kp_fit = (long long)((cap - fixed) / per_k) / TK * TK;
   int KP = (int)(kp_fit < KP_MAX ? kp_fit : KP_MAX);
   if (KP < TK) return GEP_ERR_ALLOC;
-  static unsigned long long attr_devices = 0;
-  if (first_use_on_device(attr_devices)) {
-    cudaFuncSetAttribute(k_oz_gemm<8, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes_for(MAXS));
-    cudaFuncSetAttribute(k_oz_gemm<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes_for(MAXS));
-    cudaFuncSetAttribute(k_oz_gemm<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes_for(MAXS));
-  }
   int lower = (uplo == 'L' || uplo == 'l');
   // balanced leading digits where a level may hold up to 8 digit products (see the top)
   const int xbit = levels >= 8 ? 1 : 0;
@@ -822,16 +936,9 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
     GEP_CHECK(encode_map(&mA, As, kpad, m, S, TM));
     GEP_CHECK(encode_map(&mB, Bs, kpad, n, S, TN));
     OzArgs a;
-    a.m = m; a.n = n; a.kpad = kpad; a.S = S; a.lmax = levels; a.lower = lower; a.xbit = xbit;
-    a.ea = ea; a.eb = eb; a.alpha = alpha; a.beta = (kb == 0) ? beta : 1.0; a.C = C; a.ldc = ldc; a.st = h->d_status;
-    const int gx = (m + TM - 1) / TM, gy = (n + TN - 1) / TN;
-    a.gx = gx;
-    a.gy = gy;
-    a.ntiles = gx * gy;
-    a.kr_n = 0;
-    for (int r = 0; r < OZ_KR_MAX; ++r) a.kr_lo[r] = a.kr_hi[r] = 0;
+    oz_args_init(a, m, n, kpad, S, levels, lower, xbit, ea, eb, alpha, (kb == 0) ? beta : 1.0, C, ldc, h->d_status);
     if (kr && kr->n > 0) {  // this panel's k-steps of each listed row tile
-      a.kr_n = min(min(kr->n, OZ_KR_MAX), gx);
+      a.kr_n = min(min(kr->n, OZ_KR_MAX), a.gx);
       for (int r = 0; r < a.kr_n; ++r) {
         int lo = max(kr->lo[r] - kb, 0), hi = min(kr->hi[r] - kb, kc);
         if (hi <= lo) lo = hi = 0;
@@ -839,29 +946,7 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
         a.kr_hi[r] = (short)((hi + TK - 1) / TK);
       }
     }
-    dim3 grid(a.ntiles < h->sm_count ? a.ntiles : h->sm_count);  // persistent CTAs
-    int slot = -1;
-    if (h->prof_on) {
-      if (h->prof_used < h->prof_cap) {
-        slot = h->prof_used++;
-        cudaEventRecord(h->prof_ev[2 * slot], h->stream);
-        int npairs = 0;
-        for (int s = 1; s <= S; ++s) npairs += max(0, min(S, levels - s));
-        double f = 2.0 * m * n * (double)kc * (lower ? 0.5 : 1.0);
-        h->prof_f64eq[slot] = f;
-        h->prof_flops[slot] = f * npairs;
-        h->prof_mnk[3 * slot] = m;
-        h->prof_mnk[3 * slot + 1] = n;
-        h->prof_mnk[3 * slot + 2] = kc;
-      } else {
-        h->prof_skipped++;
-      }
-    }
-    if (S == 8 && levels == 9) k_oz_gemm<8, 9><<<grid, NTHREADS, smem_bytes_for(S), h->stream>>>(mA, mB, a);
-    else if (S == 3 && levels == 4) k_oz_gemm<3, 4><<<grid, NTHREADS, smem_bytes_for(S), h->stream>>>(mA, mB, a);
-    else k_oz_gemm<0, 0><<<grid, NTHREADS, smem_bytes_for(S), h->stream>>>(mA, mB, a);
-    GEP_CHECK(check_launch(h));
-    if (slot >= 0) cudaEventRecord(h->prof_ev[2 * slot + 1], h->stream);
+    GEP_CHECK(oz_launch(h, mA, mB, a, kc));
   }
   return GEP_OK;
 }

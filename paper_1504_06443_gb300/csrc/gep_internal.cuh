@@ -133,6 +133,23 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
              const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
              int levels, const OzKRange* kr = nullptr);
 size_t oz_workspace_bytes(int m, int n, int k);
+// Digit planes of a symmetric operand (the lower triangle of an m x m matrix), split once
+// for all its K panels so that several products can share them (the two C22 products of a
+// panel pair in the full -> band reduction).  Panel p: planes + p * S * m * OZ_SYM_KP,
+// its row exponent fields at ea + p * m.
+constexpr int OZ_SYM_KP = 4096;
+struct OzSymPlanes {
+  unsigned short* planes = nullptr;
+  int* ea = nullptr;
+  int m = 0, levels = 0;
+};
+size_t oz_sym_planes_bytes(int m, int levels);
+int oz_split_sym(gep_handle_t h, int m, const double* A, int lda, int levels, void* buf, size_t bytes,
+                 OzSymPlanes* P);
+// C (m - row0 x n) = alpha A(row0:m, 0:m) B + beta C with A given by its planes P (B is
+// m x n, column-major, ld ldb): rows row0.. of the symmetric operand against all of K.
+int dgemm_oz_sym_planes(gep_handle_t h, const OzSymPlanes& P, int row0, int n, double alpha, const double* B,
+                        int ldb, double beta, double* C, int ldc);
 
 // ---- small dense helpers (blas_util.cu) ----
 int copy_matrix(gep_handle_t h, int m, int n, const double* src, int lds, double* dst, int ldd);
