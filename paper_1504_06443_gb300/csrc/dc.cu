@@ -368,11 +368,11 @@ __global__ void __launch_bounds__(256) k_secular(DcWs w, const int* st) {
   double tau = 0.5 * (lo + hi);
   for (int it = 0; it < 400; ++it) {
     double pL = 0.0, dpL = 0.0, pR = 0.0, dpR = 0.0;
-    for (int i = lane; i < k; i += 32) {
-      double del = (dd[i] - dorg) - tau;
-      double t = zz[i] * zz[i] / del;
-      if (i <= j) { pL += t; dpL += t / del; }
-      else { pR += t; dpR += t / del; }
+    for (int i = lane; i < k; i += 32) {  // one reciprocal per pole (the FP64 pipe is the bound)
+      double r = 1.0 / ((dd[i] - dorg) - tau);
+      double t = zz[i] * zz[i] * r;
+      if (i <= j) { pL += t; dpL += t * r; }
+      else { pR += t; dpR += t * r; }
     }
     pL = rho * warp_sum(pL);
     dpL = rho * warp_sum(dpL);
@@ -422,6 +422,16 @@ __global__ void __launch_bounds__(256) k_secular(DcWs w, const int* st) {
   }
 }
 
+// x <- x 2^-s with |x 2^-s| in [1, 2) (sign kept), e += s; zero and subnormal x are left as
+// they are (a zero product stays zero).
+__device__ __forceinline__ void renorm_exp(double& x, int& e) {
+  const long long bits = __double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  if (E == 0 || E == 0x7FF) return;
+  x = __longlong_as_double((bits & ~(0x7FFll << 52)) | (1023ll << 52));
+  e += E - 1023;
+}
+
 // Loewner formula: zhat_i^2 = ((lam_i - d_i)/rho) prod_{j != i} (lam_j - d_i)/(d_j - d_i).
 __global__ void k_zhat(DcWs w, const int* st) {
   if (status_bad(st)) return;
@@ -429,12 +439,22 @@ __global__ void k_zhat(DcWs w, const int* st) {
   int k = w.cnt[0];
   if (i >= k) return;
   const double di = w.ndd[i];
-  double prod = -((di - w.ndd[w.org[i]]) - w.tauR[i]) / w.rho[0];
+  // numerator and denominator products kept apart (one division at the end); every eighth
+  // factor both are brought back to [1, 2) in magnitude, their binary exponents counted in
+  // en, ed, so that neither over- nor underflows
+  double pn = -((di - w.ndd[w.org[i]]) - w.tauR[i]) / w.rho[0], pd = 1.0;
+  int en = 0, ed = 0, c = 0;
   for (int j = 0; j < k; ++j) {
     if (j == i) continue;
-    double num = -((di - w.ndd[w.org[j]]) - w.tauR[j]);
-    prod *= num / (w.ndd[j] - di);
+    pn *= -((di - w.ndd[w.org[j]]) - w.tauR[j]);
+    pd *= w.ndd[j] - di;
+    if (++c == 8) {
+      c = 0;
+      renorm_exp(pn, en);
+      renorm_exp(pd, ed);
+    }
   }
+  const double prod = ldexp(pn / pd, en - ed);
   w.zhat[i] = copysign(sqrt(fmax(prod, 0.0)), w.ndz[i]);
 }
 

@@ -210,6 +210,35 @@ __global__ void __launch_bounds__(256) k_split_rows(int R, int K, int Kpad, cons
   }
 }
 
+// The same for few rows (fewer than can fill the GPU one warp per row): one CTA per row,
+// the exponent pass reduced over the CTA.
+__global__ void __launch_bounds__(256) k_split_row_blk(int R, int K, int Kpad, const double* __restrict__ X,
+                                                       long long sr, int* __restrict__ e_out, int S, int xbit,
+                                                       unsigned short* __restrict__ out, const int* st) {
+  __shared__ int red[8];
+  if (status_bad(st)) return;
+  const int r = blockIdx.x;
+  if (r >= R) return;
+  const double* x = X + (size_t)r * sr;
+  int m = 0;
+  for (int kk = threadIdx.x; kk < K; kk += 256) m = max(m, exp_field(x[kk]));
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = red[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) m = max(m, red[w]);
+  const int e = scale_exp(m, xbit);
+  if (threadIdx.x == 0) e_out[r] = m;
+  const size_t plane = (size_t)R * Kpad;
+  for (int k0 = 4 * threadIdx.x; k0 < Kpad; k0 += 1024) {
+    double v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = (k0 + u < K) ? x[k0 + u] : 0.0;
+    split4_store(v, k0, K, e, S, (size_t)r * Kpad + k0, plane, out);
+  }
+}
+
 // Symmetric operand given by its lower triangle (op(A) = A, A(i, kk) = C(max, min)), K
 // panel [kb, kb + kc): exponents in two passes (the part of row i left of the diagonal,
 // read down the rows; then the part of column i below it, read along the column), and
@@ -741,6 +770,17 @@ int encode_map(CUtensorMap* map, const void* base, int kpad, int rows, int S, in
 
 namespace {
 
+// Exponent pass and split of an operand with contiguous K: one warp per row, or one CTA per
+// row when the rows are too few to fill the GPU that way.
+int split_rows(gep_handle_t h, int R, int K, int Kpad, const double* X, long long sr, int* e, int S, int xbit,
+               unsigned short* out) {
+  if (R < 16 * h->sm_count)
+    k_split_row_blk<<<R, 256, 0, h->stream>>>(R, K, Kpad, X, sr, e, S, xbit, out, h->d_status);
+  else
+    k_split_rows<<<(R * 32 + 255) / 256, 256, 0, h->stream>>>(R, K, Kpad, X, sr, e, S, xbit, out, h->d_status);
+  return check_launch(h);
+}
+
 // Product-kernel launch for one K panel (kc deep, planes padded to a.kpad): dynamic shared
 // memory attribute, optional per-launch timing, template dispatch on the plane/level counts.
 int oz_launch(gep_handle_t h, const CUtensorMap& mA, const CUtensorMap& mB, const OzArgs& a, int kc) {
@@ -842,9 +882,7 @@ int dgemm_oz_sym_planes(gep_handle_t h, const OzSymPlanes& P, int row0, int n, d
   for (int p = 0; p < np; ++p) {
     const int kb = p * OZ_SYM_KP, kc = min(OZ_SYM_KP, K - kb), kpad = (kc + TK - 1) / TK * TK;
     const unsigned short* As = P.planes + (size_t)p * S * P.m * OZ_SYM_KP;
-    k_split_rows<<<(n * 32 + 255) / 256, 256, 0, h->stream>>>(n, kc, kpad, B + kb, ldb, eb, S, xbit, Bs,
-                                                              h->d_status);
-    GEP_CHECK(check_launch(h));
+    GEP_CHECK(split_rows(h, n, kc, kpad, B + kb, ldb, eb, S, xbit, Bs));
     CUtensorMap mA, mB;
     GEP_CHECK(encode_map(&mA, As + (size_t)row0 * kpad, kpad, m, S, TM, P.m));  // rows row0.. of each plane
     GEP_CHECK(encode_map(&mB, Bs, kpad, n, S, TN));
@@ -910,8 +948,9 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
       GEP_CHECK(check_launch(h));
       k_split_sym<<<dim3(kpad / 32, (m + 31) / 32), 256, 0, h->stream>>>(m, kc, kpad, kb, A, lda, ea, S, xbit, As,
                                                                          h->d_status);
+      GEP_CHECK(check_launch(h));
     } else if (ska == 1) {
-      k_split_rows<<<(m * 32 + 255) / 256, 256, 0, h->stream>>>(m, kc, kpad, Ap, sra, ea, S, xbit, As, h->d_status);
+      GEP_CHECK(split_rows(h, m, kc, kpad, Ap, sra, ea, S, xbit, As));
     } else {
       GEP_CUDA(cudaMemsetAsync(ea, 0, sizeof(int) * (size_t)m, h->stream));
       k_rowexp_slab<<<dim3((m + 255) / 256, (kc + 127) / 128), 256, 0, h->stream>>>(m, kc, Ap, sra, ska, ea,
@@ -919,10 +958,10 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
       GEP_CHECK(check_launch(h));
       k_split<<<dim3(kpad / 32, (m + 31) / 32), 256, 0, h->stream>>>(m, kc, kpad, Ap, sra, ska, ea, S, xbit, As,
                                                                      h->d_status);
+      GEP_CHECK(check_launch(h));
     }
-    GEP_CHECK(check_launch(h));
     if (skb == 1) {
-      k_split_rows<<<(n * 32 + 255) / 256, 256, 0, h->stream>>>(n, kc, kpad, Bp, srb, eb, S, xbit, Bs, h->d_status);
+      GEP_CHECK(split_rows(h, n, kc, kpad, Bp, srb, eb, S, xbit, Bs));
     } else {
       GEP_CUDA(cudaMemsetAsync(eb, 0, sizeof(int) * (size_t)n, h->stream));
       k_rowexp_slab<<<dim3((n + 255) / 256, (kc + 127) / 128), 256, 0, h->stream>>>(n, kc, Bp, srb, skb, eb,
@@ -930,8 +969,8 @@ int dgemm_oz(gep_handle_t h, char ta, char tb, char uplo, int m, int n, int k, d
       GEP_CHECK(check_launch(h));
       k_split<<<dim3(kpad / 32, (n + 31) / 32), 256, 0, h->stream>>>(n, kc, kpad, Bp, srb, skb, eb, S, xbit, Bs,
                                                                      h->d_status);
+      GEP_CHECK(check_launch(h));
     }
-    GEP_CHECK(check_launch(h));
     CUtensorMap mA, mB;
     GEP_CHECK(encode_map(&mA, As, kpad, m, S, TM));
     GEP_CHECK(encode_map(&mB, Bs, kpad, n, S, TN));
