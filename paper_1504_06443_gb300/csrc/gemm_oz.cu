@@ -115,29 +115,46 @@ __device__ __forceinline__ unsigned f32_bits_of_int(int d, int bias) {
 // Balanced base-128 digits of the fixed-point integer F (|F| < 2^(7S)): d_S..d_2 in
 // [-64, 63] and the leading d_1 (the same digits the peel "d = F mod 128 in [-64, 63],
 // F <- (F - d) / 128" gives, from the least significant end).  With the offset above they
-// are plain bit fields of F + offset, so no carries are propagated.  f[0] holds d_1.
-template <int S>
-__device__ __forceinline__ void digit_bits(long long F, unsigned* f) {
-  const long long Fp = F + digit_offset<S>();
-  f[0] = f32_bits_of_int((int)(Fp >> (7 * (S - 1))), 0);
-#pragma unroll
-  for (int s = 1; s < S; ++s) f[s] = f32_bits_of_int((int)((Fp >> (7 * (S - 1 - s))) & 127), -64);
+// are plain bit fields of Fp = F + offset, so no carries are propagated: d_1 = Fp >> 7(S-1)
+// and d_s + 64 = (Fp >> 7(S-s)) & 127 for s >= 2.
+
+// BF16 pair (lo, hi halves) of the digits d' - 64 from p = 0x4300 + d' in each half, d' in
+// [0, 128]: 0x4300 + d' is the BF16 pattern of 128 + d' (exponent 2^7, mantissa d'), and
+// subtracting 192 leaves d' - 64 exactly, two digits per instruction.
+__device__ __forceinline__ unsigned bf16x2_minus192(unsigned p) {
+  unsigned r;
+  asm("sub.rn.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(p), "r"(0x43404340u));
+  return r;
 }
 
 // Digits of 4 consecutive elements x[0..3] of row r (columns kk .. kk+3, all < Kpad;
-// columns >= K are zero) written as one 8-byte store per plane; the BF16 patterns (upper
-// halves of the FP32 patterns) are paired by byte permutes.
+// columns >= K are zero) written as one 8-byte store per plane.  The leading digit (range
+// [-128, 128] in the FP32-grade setting) goes through the FP32 pattern above, paired by byte
+// permutes; the others, 7-bit fields d_s + 64 of F + offset, through the BF16 pair trick.
 template <int SC>
 __device__ __forceinline__ void split4_store_t(const double* x, int kk, int K, int e, size_t base, size_t plane,
                                                unsigned short* __restrict__ out) {
-  unsigned f[4][SC];
+  long long Fp[4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) digit_bits<SC>((kk + u < K) ? to_fixed(x[u], e, SC) : 0ll, f[u]);
+  for (int u = 0; u < 4; ++u) Fp[u] = ((kk + u < K) ? to_fixed(x[u], e, SC) : 0ll) + digit_offset<SC>();
+  {
+    unsigned f[4];
 #pragma unroll
-  for (int s = 0; s < SC; ++s) {
+    for (int u = 0; u < 4; ++u) f[u] = f32_bits_of_int((int)(Fp[u] >> (7 * (SC - 1))), 0);
     uint2 w;
-    w.x = __byte_perm(f[0][s], f[1][s], 0x7632);
-    w.y = __byte_perm(f[2][s], f[3][s], 0x7632);
+    w.x = __byte_perm(f[0], f[1], 0x7632);
+    w.y = __byte_perm(f[2], f[3], 0x7632);
+    *reinterpret_cast<uint2*>(out + base) = w;
+  }
+#pragma unroll
+  for (int s = 1; s < SC; ++s) {
+    const int sh = 7 * (SC - 1 - s);
+    unsigned a[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a[u] = (unsigned)(Fp[u] >> sh) & 127u;
+    uint2 w;
+    w.x = bf16x2_minus192(0x43004300u + (a[0] | (a[1] << 16)));
+    w.y = bf16x2_minus192(0x43004300u + (a[2] | (a[3] << 16)));
     *reinterpret_cast<uint2*>(out + base + (size_t)s * plane) = w;
   }
 }
