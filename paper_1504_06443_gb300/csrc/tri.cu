@@ -18,16 +18,27 @@ constexpr int NB = 128;  // diagonal block order
 // In-place inverse of the r x r lower triangular S (shared, leading dim NB),
 // from the bottom-right: column j of L^-1 is -(1/l_jj) * L22^-1 * l(j+1:, j).
 __device__ void tri_inv_smem(double* S, double* tmp, int r) {
+  // X = L^-1 column by column from the last: X(i, j) = -X(j, j) sum_{q=j+1..i} X(i, q) L(q, j),
+  // columns q > j already inverted in place.  Two threads per row i (lanes 2i, 2i + 1 take
+  // alternate q) halve the dependent FMA chain of each dot product.
+  const int i = threadIdx.x >> 1, part = threadIdx.x & 1;
   for (int j = r - 1; j >= 0; --j) {
     __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < r; i += blockDim.x) {
-      double s = 0.0;
-      for (int q = j + 1; q <= i; ++q) s = fma(S[i + q * NB], S[q + j * NB], s);
-      tmp[i] = s;
+    double s = 0.0, s2 = 0.0;  // two independent FMA chains per thread
+    if (i > j && i < r) {
+      int q = j + 1 + part;
+      for (; q + 2 <= i; q += 4) {
+        s = fma(S[i + q * NB], S[q + j * NB], s);
+        s2 = fma(S[i + (q + 2) * NB], S[q + 2 + j * NB], s2);
+      }
+      if (q <= i) s = fma(S[i + q * NB], S[q + j * NB], s);
     }
+    s += s2;
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    if (part == 0 && i > j && i < r) tmp[i] = s;
     __syncthreads();
     double ajj = 1.0 / S[j + j * NB];
-    for (int i = j + 1 + threadIdx.x; i < r; i += blockDim.x) S[i + j * NB] = -ajj * tmp[i];
+    if (part == 0 && i > j && i < r) S[i + j * NB] = -ajj * tmp[i];
     if (threadIdx.x == 0) S[j + j * NB] = ajj;
   }
   __syncthreads();
@@ -59,22 +70,39 @@ __global__ void __launch_bounds__(256) k_potrf_diag(int r, double* B, int ldb, d
     int i = idx % r, j = idx / r;
     S[i + j * NB] = (i >= j) ? B[GEP_IX(i, j, ldb)] : 0.0;
   }
+  // right-looking, one column per step; thread t owns row i = t mod 128 of the trailing
+  // triangle, columns of parity t / 128 (no index division, no idle upper half)
+  __shared__ double rinv;
+  const int i = threadIdx.x & (NB - 1), h = threadIdx.x / NB;
   for (int j = 0; j < r; ++j) {
     __syncthreads();
     if (threadIdx.x == 0) {
       double p = S[j + j * NB];
       if (!(p > 0.0) || !isfinite(p)) fail = j + 1;
-      else S[j + j * NB] = sqrt(p);
+      else {
+        const double l = sqrt(p);
+        S[j + j * NB] = l;
+        rinv = 1.0 / l;
+      }
     }
     __syncthreads();
     if (fail) break;
-    double ljj = S[j + j * NB];
-    for (int i = j + 1 + threadIdx.x; i < r; i += blockDim.x) S[i + j * NB] /= ljj;
+    if (h == 0 && i > j && i < r) S[i + j * NB] *= rinv;
     __syncthreads();
-    int w = r - j - 1;
-    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
-      int ii = j + 1 + t % w, cc = j + 1 + t / w;
-      if (ii >= cc) S[ii + cc * NB] = fma(-S[ii + j * NB], S[cc + j * NB], S[ii + cc * NB]);
+    if (i > j && i < r) {
+      const double lij = S[i + j * NB];
+      int c = j + 1;
+      if ((c & 1) != h) ++c;
+      for (; c + 6 <= i; c += 8) {  // four columns at a time: loads issued before the stores
+        const double l0 = S[c + j * NB], l1 = S[c + 2 + j * NB], l2 = S[c + 4 + j * NB], l3 = S[c + 6 + j * NB];
+        double* x = S + i + c * NB;
+        const double x0 = x[0], x1 = x[2 * NB], x2 = x[4 * NB], x3 = x[6 * NB];
+        x[0] = fma(-lij, l0, x0);
+        x[2 * NB] = fma(-lij, l1, x1);
+        x[4 * NB] = fma(-lij, l2, x2);
+        x[6 * NB] = fma(-lij, l3, x3);
+      }
+      for (; c <= i; c += 2) S[i + c * NB] = fma(-lij, S[c + j * NB], S[i + c * NB]);
     }
   }
   __syncthreads();
