@@ -21,9 +21,11 @@ __device__ void tri_inv_smem(double* S, double* tmp, int r) {
   // X = L^-1 column by column from the last: X(i, j) = -X(j, j) sum_{q=j+1..i} X(i, q) L(q, j),
   // columns q > j already inverted in place.  Two threads per row i (lanes 2i, 2i + 1 take
   // alternate q) halve the dependent FMA chain of each dot product.
+  __shared__ double ajj_s;
   const int i = threadIdx.x >> 1, part = threadIdx.x & 1;
   for (int j = r - 1; j >= 0; --j) {
     __syncthreads();
+    if (threadIdx.x == 0) ajj_s = 1.0 / S[j + j * NB];  // one division per column
     double s = 0.0, s2 = 0.0;  // two independent FMA chains per thread
     if (i > j && i < r) {
       int q = j + 1 + part;
@@ -37,7 +39,7 @@ __device__ void tri_inv_smem(double* S, double* tmp, int r) {
     s += __shfl_xor_sync(0xffffffffu, s, 1);
     if (part == 0 && i > j && i < r) tmp[i] = s;
     __syncthreads();
-    double ajj = 1.0 / S[j + j * NB];
+    const double ajj = ajj_s;
     if (part == 0 && i > j && i < r) S[i + j * NB] = -ajj * tmp[i];
     if (threadIdx.x == 0) S[j + j * NB] = ajj;
   }
