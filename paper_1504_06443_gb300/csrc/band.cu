@@ -39,6 +39,7 @@ namespace {
 
 constexpr int BMAX = 64;      // largest bandwidth
 constexpr int BULGE_CTAS_PER_SM = 1;  // resident bulge-chasing CTAs per SM
+constexpr int BAND_GROUP = 4;  // panels per group of the full -> band reduction (trailing update depth 2 G b)
 constexpr int PQ_ROWS = 256;  // panel rows per CTA in the panel QR (one per thread)
 constexpr int PQ_CH = 16;     // columns per reduction chunk in the panel QR
 
@@ -729,11 +730,10 @@ size_t q2_elems(int M, int b) {
 
 size_t band_ws_elems(int M, int b) {
   size_t G = pqr_partial_ctas(M);
-  // + the digit planes of the trailing matrix (shared by the two C22 products of a panel
-  // pair) and [0; V1] (M x b)
-  size_t reduce = 2 * rr(G * BMAX) + 2 * rr(BMAX) + rr(32) + 4 * rr((size_t)M * b) + rr((size_t)M * 3 * b) +
-                  2 * rr((size_t)M * 4 * b) + 6 * rr((size_t)2 * b * b) +
-                  rr(oz_sym_planes_bytes(M, 9) / sizeof(double) + 1) + rr((size_t)M * b);
+  // + the digit planes of the trailing matrix (shared by the C22 products of a panel group)
+  size_t reduce = 2 * rr(G * BMAX) + 2 * rr(BMAX) + rr(32) + 4 * rr((size_t)M * b) +
+                  2 * rr((size_t)M * 2 * BAND_GROUP * b) + 5 * rr((size_t)2 * b * b) +
+                  rr((size_t)2 * BAND_GROUP * b * b) + rr(oz_sym_planes_bytes(M, 9) / sizeof(double) + 1);
   size_t chase = rr((size_t)2 * b * M) + rr((size_t)M);  // band + progress counters
   return reduce > chase ? reduce : chase;
 }
@@ -744,9 +744,9 @@ struct BandWs {
   double *part0, *part1, *prow0, *prow1;
   long long gcap;  // CTAs the partial-sum buffers hold
   int* bar;
-  double *V, *CV, *WVW, *V1, *W1, *AA, *BB;
+  double *V, *CV, *V1, *W1;
+  double *WV, *VW;     // n x 2 G b: [W_0 V_0 W_1 V_1 ...] and [V_0 W_0 V_1 W_1 ...] of a panel group
   double *GV, *T, *Tt, *Pm, *Ym, *Zs;
-  double* Vpad;        // [0; V1], n x b
   void* planes;        // digit planes of C22
   size_t planes_bytes;
 };
@@ -823,10 +823,12 @@ int panel_w(gep_handle_t h, int n, int b, const double* V, const double* CV, dou
 
 // S1b.  C (M x M, lower triangle) -> band of width b in C (lower), reflectors below the
 // band, tau1[j] for columns j < M - b (zero where no reflector).  The upper triangle is
-// not referenced.  Panels are taken in pairs (p, p+1): panel p+1's columns and diagonal
-// block first receive panel p's pending update, C22' V1 is formed from the not yet
-// updated matrix minus the two low-rank corrections W (V^T V1) + V (W^T V1), and both
-// updates are applied together as one rank-4b product of depth 4b.
+// not referenced.  Panels are taken in groups of up to BAND_GROUP: panel j of a group first
+// receives the pending updates of panels 0..j-1 on its columns and diagonal block, its
+// C^(j) V_j is formed from the group's not yet updated trailing matrix minus the low-rank
+// corrections sum_i W_i (V_i^T V_j) + V_i (W_i^T V_j), and all the group's updates are
+// applied together as one product of depth 2 G b (512 for G = 4, b = 64: one full exact
+// chunk of the product kernel, and one digit split of the trailing matrix per group).
 int band_reduce(gep_handle_t h, int M, double* C, int ldc, int b, double* tau1, double* ws, size_t ws_elems,
                 int eng) {
   if (b < 1 || b > BMAX) return GEP_ERR_UNSUPPORTED;
@@ -848,75 +850,83 @@ int band_reduce(gep_handle_t h, int M, double* C, int ldc, int b, double* tau1, 
   w.CV = take((size_t)M * b);
   w.V1 = take((size_t)M * b);
   w.W1 = take((size_t)M * b);
-  w.WVW = take((size_t)M * 3 * b);
-  w.AA = take((size_t)M * 4 * b);
-  w.BB = take((size_t)M * 4 * b);
+  w.WV = take((size_t)M * 2 * BAND_GROUP * b);
+  w.VW = take((size_t)M * 2 * BAND_GROUP * b);
   w.GV = take((size_t)2 * b * b);
   w.T = take((size_t)2 * b * b);
   w.Tt = take((size_t)2 * b * b);
   w.Pm = take((size_t)2 * b * b);
   w.Ym = take((size_t)2 * b * b);
-  w.Zs = take((size_t)2 * b * b);
-  w.Vpad = take((size_t)M * b);
+  w.Zs = take((size_t)2 * BAND_GROUP * b * b);
   w.planes_bytes = oz_sym_planes_bytes(M, 9);
   w.planes = take(w.planes_bytes / sizeof(double) + 1);
   const int levels = eng == GEP_PREC_MIXED_REFINED ? 4 : 9;
   for (int pb = 0; M - pb - b >= 2;) {
     const int n = M - pb - b;
+    // panels of this group: panel j (j >= 1) owns columns [(j-1) b, j b) of C22 and its
+    // reflectors act on rows [j b, n), which needs n - j b >= 2
+    const int g = std::min(BAND_GROUP, (n - 2) / b + 1);
     double* P = C + (pb + b) + (size_t)pb * ldc;
     double* C22 = C + (pb + b) + (size_t)(pb + b) * ldc;
-    double* W = w.WVW;  // [W | V | W]
-    GEP_CHECK(panel_factor(h, n, b, P, ldc, tau1 + pb, w, w.V, eng));
-    // C22 V.  On the tensor-core engines C22 is split into digit planes once and the planes
-    // serve C22b V1 below as well (C22b = C22(b:, b:) is not changed in between).
+    // V_j and W_j are kept at full height n (zero above row j b) in WV / VW, so that the
+    // pending update of panel i on any block of C22 is the same slice of one product.
+    auto wv = [&](int blk) { return w.WV + (size_t)blk * b * n; };
+    auto vw = [&](int blk) { return w.VW + (size_t)blk * b * n; };
+    // C22 is split into digit planes once for the group on the tensor-core engines: every
+    // C^(j) V_j below reads rows j b.. of the planes against the full-height V_j.  The columns
+    // the group updates in between (those of panels 1..g-1) meet V_j's zero rows.
     OzSymPlanes planes;
     const bool use_planes = eng != GEP_PREC_FP64 && n >= 128 && b >= 64;
-    if (use_planes) {
-      GEP_CHECK(oz_split_sym(h, n, C22, ldc, levels, w.planes, w.planes_bytes, &planes));
-      GEP_CHECK(dgemm_oz_sym_planes(h, planes, 0, b, 1.0, w.V, n, 0.0, w.CV, n));
-    } else {
-      GEP_CHECK(dgemm(h, 'S', 'N', 'F', n, b, n, 1.0, C22, ldc, w.V, n, 0.0, w.CV, n, eng));
+    if (use_planes) GEP_CHECK(oz_split_sym(h, n, C22, ldc, levels, w.planes, w.planes_bytes, &planes));
+    for (int j = 0; j < g; ++j) {
+      const int r0 = j * b, nr = n - r0;  // panel j's reflectors act on rows [r0, n) of C22
+      double* Vj;
+      if (j == 0) {
+        GEP_CHECK(panel_factor(h, n, b, P, ldc, tau1 + pb, w, w.V, eng));
+        Vj = w.V;
+      } else {
+        // panel j = C22 columns [(j-1) b, j b), rows [(j-1) b, n): the pending updates of
+        // panels 0..j-1 first (its diagonal block on the lower triangle only), then its QR
+        const int c0 = r0 - b;
+        double* Dj = C22 + c0 + (size_t)c0 * ldc;
+        GEP_CHECK(dgemm(h, 'N', 'T', 'L', b, b, 2 * j * b, -1.0, w.WV + c0, n, w.VW + c0, n, 1.0, Dj, ldc, eng));
+        GEP_CHECK(dgemm(h, 'N', 'T', 'F', nr, b, 2 * j * b, -1.0, w.WV + r0, n, w.VW + c0, n, 1.0, Dj + b, ldc,
+                        eng));
+        GEP_CHECK(panel_factor(h, nr, b, Dj + b, ldc, tau1 + pb + r0, w, w.V1, eng));
+        Vj = w.V1;
+      }
+      // V_j at full height into both group buffers (zero rows above r0)
+      if (r0 > 0) {
+        GEP_CHECK(set_matrix(h, r0, b, 0.0, 0.0, wv(2 * j + 1), n));
+        GEP_CHECK(set_matrix(h, r0, b, 0.0, 0.0, vw(2 * j), n));
+        GEP_CHECK(set_matrix(h, r0, b, 0.0, 0.0, wv(2 * j), n));
+        GEP_CHECK(set_matrix(h, r0, b, 0.0, 0.0, vw(2 * j + 1), n));
+      }
+      GEP_CHECK(copy_matrix(h, nr, b, Vj, nr, wv(2 * j + 1) + r0, n));
+      GEP_CHECK(copy_matrix(h, nr, b, Vj, nr, vw(2 * j) + r0, n));
+      // C^(j) V_j = C22(r0:, r0:) V_j - sum_{i<j} (W_i V_i^T + V_i W_i^T)(r0:, r0:) V_j
+      if (use_planes && nr >= 128) {
+        GEP_CHECK(dgemm_oz_sym_planes(h, planes, r0, b, 1.0, vw(2 * j), n, 0.0, w.CV, nr));
+      } else {
+        GEP_CHECK(dgemm(h, 'S', 'N', 'F', nr, b, nr, 1.0, C22 + r0 + (size_t)r0 * ldc, ldc, Vj, nr, 0.0, w.CV, nr,
+                        eng));
+      }
+      if (j > 0) {
+        // Zs = [V_0 W_0 .. V_{j-1} W_{j-1}](r0:)^T V_j, CV -= [W_0 V_0 ..](r0:) Zs
+        GEP_CHECK(dgemm(h, 'T', 'N', 'F', 2 * j * b, b, nr, 1.0, w.VW + r0, n, Vj, nr, 0.0, w.Zs, 2 * j * b, eng));
+        GEP_CHECK(dgemm(h, 'N', 'N', 'F', nr, b, 2 * j * b, -1.0, w.WV + r0, n, w.Zs, 2 * j * b, 1.0, w.CV, nr,
+                        eng));
+      }
+      GEP_CHECK(panel_w(h, nr, b, Vj, w.CV, w.W1, w, eng));
+      GEP_CHECK(copy_matrix(h, nr, b, w.W1, nr, wv(2 * j) + r0, n));
+      GEP_CHECK(copy_matrix(h, nr, b, w.W1, nr, vw(2 * j + 1) + r0, n));
     }
-    GEP_CHECK(panel_w(h, n, b, w.V, w.CV, W, w, eng));
-    GEP_CHECK(copy_matrix(h, n, b, w.V, n, w.WVW + (size_t)n * b, n));
-    GEP_CHECK(copy_matrix(h, n, b, W, n, w.WVW + (size_t)2 * n * b, n));
-    const int n1 = n - b;  // trailing order after panel p+1
-    if (n1 < 2) {
-      // C22 -= [W V] [V W]^T (lower triangle)
-      GEP_CHECK(dgemm(h, 'N', 'T', 'L', n, n, 2 * b, -1.0, w.WVW, n, w.WVW + (size_t)n * b, n, 1.0, C22, ldc, eng));
-      pb += b;
-      continue;
-    }
-    // panel p+1 = C22(b:, 0:b), its diagonal block C22(0:b, 0:b): apply panel p's update
-    double* P1 = C22 + b;
-    GEP_CHECK(dgemm(h, 'N', 'T', 'L', b, b, 2 * b, -1.0, w.WVW, n, w.WVW + (size_t)n * b, n, 1.0, C22, ldc, eng));
-    GEP_CHECK(dgemm(h, 'N', 'T', 'F', n1, b, 2 * b, -1.0, w.WVW + b, n, w.WVW + (size_t)n * b, n, 1.0, P1, ldc,
-                    eng));
-    GEP_CHECK(panel_factor(h, n1, b, P1, ldc, tau1 + pb + b, w, w.V1, eng));
-    double* C22b = C22 + b + (size_t)b * ldc;  // not yet updated by panel p
-    if (use_planes && n1 >= 128) {
-      // C22b V1 = rows b.. of C22 times [0; V1]: the planes' columns 0..b-1 (panel p+1, since
-      // updated) meet zeros
-      GEP_CHECK(set_matrix(h, b, b, 0.0, 0.0, w.Vpad, n));
-      GEP_CHECK(copy_matrix(h, n1, b, w.V1, n1, w.Vpad + b, n));
-      GEP_CHECK(dgemm_oz_sym_planes(h, planes, b, b, 1.0, w.Vpad, n, 0.0, w.CV, n1));
-    } else {
-      GEP_CHECK(dgemm(h, 'S', 'N', 'F', n1, b, n1, 1.0, C22b, ldc, w.V1, n1, 0.0, w.CV, n1, eng));
-    }
-    // Zs = [V' W']^T V1 (2b x b), CV -= [W' V'] Zs  (' = rows b.. of panel p's V, W)
-    GEP_CHECK(dgemm(h, 'T', 'N', 'F', 2 * b, b, n1, 1.0, w.WVW + (size_t)n * b + b, n, w.V1, n1, 0.0, w.Zs, 2 * b,
-                    eng));
-    GEP_CHECK(dgemm(h, 'N', 'N', 'F', n1, b, 2 * b, -1.0, w.WVW + b, n, w.Zs, 2 * b, 1.0, w.CV, n1, eng));
-    GEP_CHECK(panel_w(h, n1, b, w.V1, w.CV, w.W1, w, eng));
-    // C22b -= [W' V' W1 V1] [V' W' V1 W1]^T (lower triangle, depth 4b)
-    GEP_CHECK(copy_matrix(h, n1, 2 * b, w.WVW + b, n, w.AA, n1));                     // W' V'
-    GEP_CHECK(copy_matrix(h, n1, b, w.W1, n1, w.AA + (size_t)2 * b * n1, n1));      // W1
-    GEP_CHECK(copy_matrix(h, n1, b, w.V1, n1, w.AA + (size_t)3 * b * n1, n1));      // V1
-    GEP_CHECK(copy_matrix(h, n1, 2 * b, w.WVW + (size_t)n * b + b, n, w.BB, n1));    // V' W'
-    GEP_CHECK(copy_matrix(h, n1, b, w.V1, n1, w.BB + (size_t)2 * b * n1, n1));      // V1
-    GEP_CHECK(copy_matrix(h, n1, b, w.W1, n1, w.BB + (size_t)3 * b * n1, n1));      // W1
-    GEP_CHECK(dgemm(h, 'N', 'T', 'L', n1, n1, 4 * b, -1.0, w.AA, n1, w.BB, n1, 1.0, C22b, ldc, eng));
-    pb += 2 * b;
+    // trailing matrix after the group: C22(t0:, t0:) -= [W_0 V_0 ..][V_0 W_0 ..]^T (lower
+    // triangle, depth 2 g b), t0 = (g-1) b
+    const int t0 = (g - 1) * b, nt = n - t0;
+    GEP_CHECK(dgemm(h, 'N', 'T', 'L', nt, nt, 2 * g * b, -1.0, w.WV + t0, n, w.VW + t0, n, 1.0,
+                    C22 + t0 + (size_t)t0 * ldc, ldc, eng));
+    pb += g * b;
   }
   return GEP_OK;
 }
