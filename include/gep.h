@@ -272,6 +272,13 @@ int gep_set_wait_fault(gep_handle_t h, int drop_sweep, double wait_limit_s);
  * for any other value. */
 int gep_set_panel_qr(gep_handle_t h, int rows);
 
+/* Test hook for the panel grouping of the full -> band reduction (S1b).  Panels are taken in
+ * groups of four (their trailing updates deferred and applied as one product) while the
+ * trailing matrix has order >= min_order, in pairs below it; by default min_order = 8192.
+ * min_order = 0 groups every panel it can (so that small matrices exercise the grouped
+ * path), -1 restores the default.  Returns -2 for min_order < -1. */
+int gep_set_band_group(gep_handle_t h, int min_order);
+
 /* Per-stage times (ms) of the last gep_solve with o->timers = 1:
  * t[0] Cholesky (R1), t[1] reduction (R2), t[2] tridiagonalisation (TRD/BAND),
  * t[3] tridiagonal eigensolver (D&C), t[4] Householder back-transform (BACK),

@@ -115,6 +115,7 @@ def load():
                                                           ctypes.POINTER(_SZ)]),
             "gep_solve_batched_opts": (_I, [_P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(GepOptions), _I]),
             "gep_batched_info": (_I, [_P, ctypes.POINTER(_I)]),
+            "gep_set_band_group": (_I, [_P, _I]),
             "gep_dgemm": (_I, [_P, ctypes.c_char, ctypes.c_char, ctypes.c_char, _I, _I, _I, _D, _P, _I, _P, _I,
                                _D, _P, _I, _I]),
         }
@@ -266,6 +267,11 @@ class Handle:
         """Test hook: force the panel-QR CTA height of the full -> band reduction (64, 128 or
         256 rows per CTA), the per-column-step kernel (-1), or the automatic choice (0)."""
         _check(self.lib.gep_set_panel_qr(self.h, int(rows)), "gep_set_panel_qr")
+
+    def set_band_group(self, min_order=-1):
+        """Test hook: the trailing order from which the full -> band reduction groups panels in
+        fours (0: always, -1: the library default)."""
+        _check(self.lib.gep_set_band_group(self.h, int(min_order)), "gep_set_band_group")
 
     def stage_times(self):
         t = (_D * 7)()

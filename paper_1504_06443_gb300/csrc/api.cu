@@ -336,6 +336,13 @@ int gep_set_panel_qr(gep_handle_t h, int rows) {
   return GEP_OK;
 }
 
+int gep_set_band_group(gep_handle_t h, int min_order) {
+  if (!handle_ok(h)) return GEP_ERR_HANDLE;
+  if (min_order < -1) return -2;
+  h->band_group_min = min_order;
+  return GEP_OK;
+}
+
 long long gep_launch_count(gep_handle_t h, int reset) {
   if (!handle_ok(h)) return -1;
   long long n = h->launches;

@@ -40,6 +40,7 @@ namespace {
 constexpr int BMAX = 64;      // largest bandwidth
 constexpr int BULGE_CTAS_PER_SM = 1;  // resident bulge-chasing CTAs per SM
 constexpr int BAND_GROUP = 4;  // panels per group of the full -> band reduction (trailing update depth 2 G b)
+constexpr int BAND_GROUP_MIN_N = 8192;  // trailing order from which groups of BAND_GROUP are used
 constexpr int PQ_ROWS = 256;  // panel rows per CTA in the panel QR (one per thread)
 constexpr int PQ_CH = 16;     // columns per reduction chunk in the panel QR
 
@@ -865,7 +866,10 @@ int band_reduce(gep_handle_t h, int M, double* C, int ldc, int b, double* tau1, 
     const int n = M - pb - b;
     // panels of this group: panel j (j >= 1) owns columns [(j-1) b, j b) of C22 and its
     // reflectors act on rows [j b, n), which needs n - j b >= 2
-    const int g = std::min(BAND_GROUP, (n - 2) / b + 1);
+    // (groups pay where the trailing matrix is large; below that pairs, whose two C22 products
+    // need no cross-panel corrections beyond one pair of small products)
+    const int gmin = h->band_group_min >= 0 ? h->band_group_min : BAND_GROUP_MIN_N;
+    const int g = std::min(n >= gmin ? BAND_GROUP : 2, (n - 2) / b + 1);
     double* P = C + (pb + b) + (size_t)pb * ldc;
     double* C22 = C + (pb + b) + (size_t)(pb + b) * ldc;
     // V_j and W_j are kept at full height n (zero above row j b) in WV / VW, so that the

@@ -26,6 +26,7 @@ struct gep_handle_s {
   // test hook: rows per CTA of the single-launch panel QR (64, 128 or 256), -1 for the
   // one-launch-per-column kernel, 0 for the automatic choice
   int pqr_rows = 0;
+  int band_group_min = -1;  // trailing order from which S1b takes panels in groups of four (-1: default)
   int magic = 0x6e70;
   cudaEvent_t ev[8] = {};
   cudaEvent_t ev_band = nullptr;  // between full->band and bulge chasing (two-stage, timers on)

@@ -73,6 +73,9 @@ def test_host_checks_without_gpu(libpath):
     lib.gep_set_panel_qr.argtypes = [ctypes.c_void_p, ctypes.c_int]
     lib.gep_set_panel_qr.restype = ctypes.c_int
     assert lib.gep_set_panel_qr(None, 64) == -104
+    lib.gep_set_band_group.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.gep_set_band_group.restype = ctypes.c_int
+    assert lib.gep_set_band_group(None, 0) == -104
     lib.gep_reset_info.argtypes = [ctypes.c_void_p]
     lib.gep_reset_info.restype = ctypes.c_int
     assert lib.gep_reset_info(None) == -104

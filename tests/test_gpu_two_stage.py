@@ -223,6 +223,47 @@ def test_tridiag_2stage_spectrum_each_panel_qr_form(gep, oracle_lib, rows):
     assert np.max(np.abs(wT - w_ref)) <= 200 * M * EPS * nC
 
 
+@pytest.mark.parametrize("precision", ["fp64_emulated", "mixed_refined"])
+@pytest.mark.parametrize("M", [640, 2100])
+def test_solve_2stage_grouped_panels(gep, oracle_lib, precision, M):
+    """The full -> band reduction takes panels in groups of four (deferred trailing updates,
+    corrections to C^(j) V_j, one digit split and one depth-512 update per group) only from
+    trailing order 8192 by default; the hook groups every panel, so the grouped path and
+    its ragged last groups (640 = 9 panels + tail, 2100 = 32 panels + tail) are checked
+    against the oracle here: eigenvalues, residual, B-orthonormality, isolated eigenvectors."""
+    tb = gi.tight_binding(M, seed=M + 3)
+    A, B = tb["A"], tb["B"]
+    if M not in _ORACLE_2STAGE:
+        w_ref, Y_ref, info = oracle_lib.gep_solve(A, B)
+        assert info == 0
+        _ORACLE_2STAGE[M] = (w_ref, Y_ref, float(np.max(np.abs(np.linalg.eigvalsh(A)))))
+    w_ref, Y_ref, nA = _ORACLE_2STAGE[M]
+    h = gep.Handle()
+    h.set_band_group(0)
+    try:
+        w, Y, info = gep.solve(dev(A), dev(B), sep="2stage", precision=precision, handle=h)
+    finally:
+        h.set_band_group(-1)
+    assert info == 0
+    wh, Yh = host(w), host(Y)
+    assert np.max(np.abs(wh - w_ref)) <= 1e-11 * nA
+    res = np.linalg.norm(A @ Yh - (B @ Yh) * wh[None, :]) / (np.linalg.norm(A) * M)
+    orth = np.max(np.abs(Yh.T @ B @ Yh - np.eye(M)))
+    assert res <= 1e-13, res
+    assert orth <= 1e-12, orth
+    gaps = np.minimum(np.diff(w_ref, prepend=-np.inf), np.diff(w_ref, append=np.inf))
+    iso = gaps > 1e-6 * nA
+    assert np.max(np.abs(Yh[:, iso] - Y_ref[:, iso])) <= 1e-8
+
+
+def test_band_group_hook_rejects_bad_values(gep):
+    h = gep.Handle()
+    with pytest.raises(gep.GepError):
+        h.set_band_group(-2)
+    h.set_band_group(0)
+    h.set_band_group(-1)
+
+
 def test_panel_qr_hook_rejects_bad_values(gep):
     h = gep.Handle()
     for bad in (1, 32, 512, -2):
