@@ -105,8 +105,9 @@ typedef struct gep_options {
  * (B-Rayleigh quotients and the first-order correction X <- X (I + E) from S = X^T A X,
  * R = X^T B X formed with FP64-accurate products; pairs whose gap is below
  * max(64 |S_ij - lambda_j R_ij|, 16 max_ij |S_ij - lambda_j R_ij|, 1e-6 max|lambda|) are
- * grouped into clusters of up to 32 eigenpairs whose k x k pencil (S_CC, R_CC) is solved
- * exactly). */
+ * grouped into clusters whose k x k pencil (S_CC, R_CC) is solved exactly: by one thread
+ * up to 32 eigenpairs, by one CTA up to 256; inside larger clusters a pair takes the
+ * first-order step where its own gap is safe, else -R_ij / 2). */
 void gep_default_options(gep_options* o);
 
 /* Creates a handle bound to `stream` (a cudaStream_t passed as void*; NULL = legacy
