@@ -55,3 +55,45 @@ def test_reference_arm_under_torchrun_two_ranks():
     lines = _json_lines(r.stdout)
     assert len(lines) == 1
     _check_line(lines[0], 2)
+
+
+def _bench_module():
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench
+    return bench
+
+
+def test_stage_rooflines_counts_the_method_not_the_gpu_path():
+    """The per-stage roofline block uses the method's algorithmic flop counts: the two-stage
+    back-transformation is 4 M^3 (2 M^3 for 1-stage), the lowest-n route shrinks S3 and R3 by
+    n / M, the Cholesky-free reducer's stages are named for Eq. 7-9, and every rate is those
+    flops over the stage time (36 plane products per FP64-equivalent flop for the BF16 ratio)."""
+    b = _bench_module()
+    M = 1000
+    m3 = float(M) ** 3
+    stages = [1.0, 2.0, 4.0, 3.0, 5.0, 1.0, 0.0]
+    f64 = {"fp64_dgemm_tflops_sustained": 1.0}
+    full = b.stage_rooflines(M, stages, [3.0, 1.0], True, "2stage", 64, 1000.0, f64)
+    assert full["stages"]["S3_back_q"]["alg_flops"] == 4.0 * m3
+    assert full["stages"]["R3_backsub"]["alg_flops"] == m3
+    r1 = full["stages"]["R1_cholesky"]
+    assert abs(r1["fp64_equiv_tflops"] - (m3 / 3) / 1e-3 / 1e12) < 1e-12
+    assert abs(r1["frac_of_bf16_sustained_36_planes"] - r1["fp64_equiv_tflops"] * 36 / 1000.0) < 1e-12
+    one = b.stage_rooflines(M, stages, None, True, "1stage", 0, 1000.0, f64)
+    assert one["stages"]["S3_back_q"]["alg_flops"] == 2.0 * m3
+    half = b.stage_rooflines(M, stages, [3.0, 1.0], True, "2stage", 64, 1000.0, f64, n=M // 2)
+    assert half["stages"]["S3_back_q"]["alg_flops"] == 2.0 * m3
+    assert half["stages"]["R3_backsub"]["alg_flops"] == 0.5 * m3
+    ee = b.stage_rooflines(M, stages, [3.0, 1.0], True, "2stage", 64, 1000.0, f64, reducer="eigenexa")
+    assert set(ee["stages"]) >= {"E7_sep_of_B", "E8_A_prime", "E9_Y_is_XZ", "S3_back_q"}
+    assert ee["stages"]["E8_A_prime"]["alg_flops"] == 3.0 * m3
+    vals = b.stage_rooflines(M, stages, [3.0, 1.0], False, "2stage", 64, 1000.0, f64)
+    assert "S3_back_q" not in vals["stages"] and "R3_backsub" not in vals["stages"]
+
+
+def test_cm3_fit_recovers_a_cubic_law():
+    b = _bench_module()
+    samples = [(m, 2e-9 * m ** 3) for m in (100, 200, 300)]
+    v, c = b.cm3_fit(samples, 1000)
+    assert abs(c - 2e-9) < 1e-18 and abs(v - 2.0) < 1e-9
